@@ -1,0 +1,302 @@
+"""Pins of the FP64 oracle against things other than itself (arXiv 2207.09431).
+
+Closed forms (power-law channel, hydrostatics, Laplace law, the modified
+equation of the flat interface), conservation invariants, special cases, an
+independent brute-force NumPy stepper on tiny grids, and values printed in the
+paper's tables.  None of these runs on a GPU.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import handstep_numpy as hs
+from oracle import observables as obs
+from paper_2207_09431_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _single_phase(nx, ny, **kw):
+    p = dict(nx=nx, ny=ny, ncomp=2, rho=(1.0, 1.0, 1.0), tau=(0.8, 0.8, 0.8))
+    p.update(kw)
+    o = oracle.Oracle(p)
+    o.set_fields(np.ones((1, ny, nx)))
+    return o
+
+
+# ------------------------------------------------------------------ P1
+@pytest.mark.parametrize("n", [0.5, 0.8, 1.0, 1.5])
+def test_powerlaw_channel_closed_form(n):
+    """Sec. 3.2 / Eq. 34: body-force driven power-law channel between walls.
+
+    Force balance k |du/dy|^n = F |y| gives u(y) = n/(n+1) (F/k)^(1/n)
+    (H^((n+1)/n) - |y|^((n+1)/n)), the paper's profile with u_in its mean.
+    Pins Eq. 25-33 (strain rate from the non-equilibrium part, power-law tau)."""
+    table = _golden("paper_table2_channel.json")
+    bound = dict(zip(table["n"], table["E_rel"]))[n]
+    Ny, H, umax = 60, 30.0, 0.02
+    r = (umax * (n + 1) / n / H ** ((n + 1) / n)) ** n   # F / k
+    k = 0.8 / 3.0 / (r * H) ** ((n - 1.0) / n)             # tau = 0.8 at the wall
+    F = r * k
+    o = _single_phase(2, Ny, powerlaw=1, pl_n=n, pl_k=k, tau_min=0.02, tau_max=20.0, force_x=F)
+    prev = None
+    for _ in range(200):
+        o.step(500)
+        u = o.field("ux")[:, 0]
+        # steady-state criterion in the spirit of Sec. 3.3
+        if prev is not None and np.linalg.norm(u - prev) / np.linalg.norm(u) < 1e-9:
+            break
+        prev = u
+    y = np.arange(Ny) + 0.5 - H
+    ua = n / (n + 1) * (F / k) ** (1 / n) * (H ** ((n + 1) / n) - np.abs(y) ** ((n + 1) / n))
+    err = np.linalg.norm(u - ua) / np.linalg.norm(ua)          # Eq. 35
+    assert err <= bound
+    # the strain rate the method computes locally vs |du/dy| of the closed form
+    gd = o.field("shear")[:, 0]
+    gda = (F * np.abs(y) / k) ** (1 / n)
+    away = np.abs(y) > 5
+    assert np.max(np.abs(gd[away] - gda[away]) / gda[away]) < 0.02
+
+
+# ------------------------------------------------------------------ P8
+def test_hydrostatic_pressure():
+    """Gravity on a resting single phase between walls: p linear with slope -rho g."""
+    g = 1e-5
+    o = _single_phase(4, 40, gravity=g)
+    o.step(20000)
+    p = o.field("p")[:, 0]
+    y = np.arange(40)
+    slope, icpt = np.polyfit(y, p, 1)
+    assert abs(slope + g) / g < 1e-6
+    assert np.max(np.abs(p - (slope * y + icpt))) < 1e-6 * g * 40
+    assert np.max(np.abs(o.field("uy"))) < 1e-12
+
+
+# ------------------------------------------------------------------ P2
+def test_laplace_law():
+    """Static 2-D bubble: the pressure jump is sigma / R (the interface tension
+    sigma_ij follows from the scaling of Eq. 2-5)."""
+    sigma = 1e-3
+    Rs, dps = [], []
+    for R in (8.0, 10.0, 12.0):
+        p = dict(nx=48, ny=48, ncomp=2, periodic_y=1, rho=(1.0, 1.0, 1.0), tau=(0.5, 0.5, 0.5),
+                 sigma12=sigma, sigma13=sigma, sigma23=sigma, xi=4.0, D0=4.0 / 300.0)
+        o = oracle.Oracle(p)
+        o.init_bubbles([[24, 24, R, 3]])
+        o.step(3000)
+        pr = o.field("p")
+        Reff = math.sqrt(o.observables()["area"] / math.pi)
+        Rs.append(Reff)
+        dps.append(pr[24, 24] - pr[0, 0])
+        assert np.max(np.hypot(o.field("ux"), o.field("uy"))) < 1e-5
+    slope = np.polyfit(1.0 / np.array(Rs), np.array(dps), 1)[0]
+    assert abs(slope - sigma) / sigma < 0.05
+
+
+# ------------------------------------------------------------------ P3
+def test_chemical_potential_vanishes_on_tanh_profile():
+    """The flat tanh profile of width xi (the shape of Eq. 42) is stationary for
+    the free energy of Eq. 2-3: mu_1 - mu_3 (the potential of C1 when C2 = 0)
+    vanishes up to the stencil error, here made small with a wide interface."""
+    xi, sigma, nx = 24.0, 1e-3, 256
+    p = dict(nx=nx, ny=2, ncomp=2, periodic_y=1, sigma12=sigma, sigma13=sigma, sigma23=sigma, xi=xi)
+    o = oracle.Oracle(p)
+    x = np.arange(nx, dtype=float)
+    C = 0.5 + 0.5 * np.tanh(2 * (x - 64) / xi) - (0.5 + 0.5 * np.tanh(2 * (x - 192) / xi))
+    o.set_fields(np.tile(C, (2, 1))[None])
+    mu = o.field("mu1")[0] - o.field("mu3")[0]
+    scale = 12 * sigma / xi          # magnitude of the double-well term
+    assert np.max(np.abs(mu)) < 2e-3 * scale
+    # a profile twice too wide is far from stationary
+    C2 = 0.5 + 0.5 * np.tanh((x - 64) / xi) - (0.5 + 0.5 * np.tanh((x - 192) / xi))
+    o.set_fields(np.tile(C2, (2, 1))[None])
+    mu2 = o.field("mu1")[0] - o.field("mu3")[0]
+    assert np.max(np.abs(mu2)) > 0.1 * scale
+
+
+@pytest.mark.parametrize("D0", [4.0 / 300.0, 0.01])
+def test_flat_interface_width_modified_equation(D0):
+    """Flat interface dynamics.  With tau_h = 1/2 the collision of Eq. 18 sets
+    h to its equilibrium, and streaming plus the central directional derivative
+    add -(1/24) lap^2 C per step (Taylor expansion of the D2Q9 shift); the CH
+    equation then has gradient coefficient (3/4) xi + 1/(24 D0), so the
+    stationary tanh widens to xi sqrt(1 + 1/(18 D0 xi)).  A sign slip in the
+    half forcing of Eq. 18-20 turns this into second-order diffusion."""
+    xi, nx = 4.0, 64
+    p = dict(nx=nx, ny=2, ncomp=2, periodic_y=1, xi=xi, D0=D0)
+    o = oracle.Oracle(p)
+    x = np.arange(nx, dtype=float)
+    C = 0.5 + 0.5 * np.tanh(2 * (x - 16) / xi) - (0.5 + 0.5 * np.tanh(2 * (x - 48) / xi))
+    o.set_fields(np.tile(C, (2, 1))[None])
+    o.step(4000)
+    c = o.field("C1")[0]
+    width = 1.0 / np.max(np.gradient(c))       # tanh(2x/w)/2 has slope 1/w at its centre
+    pred = xi * math.sqrt(1.0 + 1.0 / (18.0 * D0 * xi))
+    assert abs(width - pred) / pred < 0.05
+    assert abs(c.sum() - C.sum()) < 1e-10
+
+
+# ------------------------------------------------------------------ P4
+def test_mass_conservation_constant_mobility():
+    """Constant mobility: every source of Eq. 18 sums to zero over directions
+    and the discrete Laplacian telescopes (mirror ghosts at walls), so each
+    component's mass is conserved to round-off."""
+    p, b = inputs.small_case(mobility=0)
+    p = dict(p, nx=32, ny=64)
+    o = oracle.Oracle(p)
+    o.init_bubbles([[16, 20, 6, 3]], seed=1, noise=1e-8)
+    m0 = o.observables()["mass"]
+    o.step(300)
+    m1 = o.observables()["mass"]
+    nodes = p["nx"] * p["ny"]
+    for i in (0, 2):
+        # round-off of a sum of `nodes` values of order 1, over 300 steps
+        assert abs(m1[i] - m0[i]) < 1e-13 * nodes
+
+
+def test_mass_balance_variable_mobility():
+    """Variable mobility: the split form of Eq. 21 is not a discrete divergence,
+    so mass changes by exactly the summed diffusion sources per step."""
+    p, b = inputs.small_case(mobility=1)
+    p = dict(p, nx=32, ny=64)
+    o = oracle.Oracle(p)
+    o.init_bubbles([[16, 20, 6, 3]], seed=1, noise=1e-8)
+    o.step(50)
+    for _ in range(5):
+        m0 = o.observables()["mass"][0]
+        o.step(1)
+        src = o.field("S")[0].sum() + o.field("V")[0].sum()
+        m1 = o.observables()["mass"][0]
+        assert abs((m1 - m0) - src) < 1e-12 * abs(m0)
+
+
+# ------------------------------------------------------------------ P5
+def test_binary_reduction_three_sets():
+    """With C2 = 0 the chemical potential mu_2 vanishes (Sigma_1 + Sigma_3 =
+    2 sigma_13), so a three-set run stays binary and equals the two-set run."""
+    p, b = inputs.small_case(mobility=0)
+    p2 = dict(p, nx=24, ny=48, sigma12=1.2e-3, sigma23=0.9e-3)
+    C = inputs.bubble_fields(24, 48, 2, 4.0, [(12, 16, 6, 3)], seed=2, noise=1e-8)
+    a = oracle.Oracle(p2)
+    a.set_fields(C)
+    p3 = dict(p2, ncomp=3)
+    b3 = oracle.Oracle(p3)
+    b3.set_fields(np.stack([C[0], np.zeros_like(C[0])]))
+    a.step(200)
+    b3.step(200)
+    assert np.max(np.abs(b3.field("C2"))) < 1e-14
+    for f in ("C1", "p", "ux", "uy", "tau"):
+        x, y = a.field(f), b3.field(f)
+        # 200 steps of round-off through the power law (pow of a small shear rate)
+        assert np.max(np.abs(x - y)) <= 1e-10 * max(1.0, np.max(np.abs(x)))
+
+
+# ------------------------------------------------------------------ P6
+@pytest.mark.parametrize("periodic_y", [1, 0])
+@pytest.mark.parametrize("ncomp", [2, 3])
+@pytest.mark.parametrize("mobility", [0, 1])
+@pytest.mark.parametrize("fd_scheme", [0, 1])
+@pytest.mark.parametrize("powerlaw", [0, 1])
+def test_hand_step_4x4(periodic_y, ncomp, mobility, fd_scheme, powerlaw):
+    """Brute force: an independent vectorised NumPy restatement of the step
+    (tests/handstep_numpy.py) on a 4 x 4 grid for 3 steps."""
+    rng = np.random.default_rng(100 + 16 * periodic_y + 8 * ncomp + 4 * mobility + 2 * fd_scheme + powerlaw)
+    P = dict(oracle.DEFAULTS)
+    P.update(nx=4, ny=4, ncomp=ncomp, periodic_y=periodic_y, rho=(1.0, 0.5, 0.1),
+             tau=(0.6, 0.7, 0.55), powerlaw=powerlaw, pl_n=0.7, pl_k=0.05, gravity=1e-3,
+             force_x=2e-4, mobility=mobility, fd_scheme=fd_scheme, D0=0.01, sigma12=1e-3,
+             sigma13=1.5e-3, sigma23=2e-3)
+    C = np.zeros((ncomp - 1, 4, 4))
+    C[0] = 0.5 + 0.4 * rng.random((4, 4))
+    if ncomp == 3:
+        C[1] = 0.3 * rng.random((4, 4))
+    o = oracle.Oracle(P)
+    o.set_fields(C)
+    g, h, tau = hs.init_state(P, C)
+    assert np.max(np.abs(o.field("g") - g)) < 1e-15
+    assert np.max(np.abs(o.field("h") - h)) < 1e-15
+    for _ in range(3):
+        o.step(1)
+        g, h, tau = hs.step(P, g, h, tau)
+    assert np.max(np.abs(o.field("g") - g)) < 1e-11
+    assert np.max(np.abs(o.field("h") - h)) < 1e-11
+    assert np.max(np.abs(o.field("tau") - tau)) < 1e-11
+
+
+# ------------------------------------------------------------------ P7
+def test_uniform_rest_state_is_fixed_point():
+    o = _single_phase(6, 5)
+    g0 = o.field("g")
+    o.step(50)
+    assert np.max(np.abs(o.field("g") - g0)) < 1e-15
+
+
+def test_newtonian_power_law_equals_fixed_tau():
+    """n = 1 turns Eq. 31 into eta = k, i.e. tau = k / (rho cs^2)."""
+    k = 0.25
+    a = _single_phase(2, 20, powerlaw=1, pl_n=1.0, pl_k=k, tau_max=10.0, force_x=1e-6)
+    b = _single_phase(2, 20, tau=(3 * k, 3 * k, 3 * k), force_x=1e-6)
+    a.step(500)
+    b.step(500)
+    assert np.max(np.abs(a.field("ux") - b.field("ux"))) < 1e-13 * np.max(np.abs(b.field("ux")))
+
+
+def test_mirror_symmetry_of_centred_bubble():
+    p, _ = inputs.small_case(mobility=1)
+    p = dict(p, nx=32, ny=48)
+    o = oracle.Oracle(p)
+    o.set_fields(inputs.bubble_fields(32, 48, 2, 4.0, [(15.5, 16, 7, 3)]))
+    o.step(100)
+    ux, uy = o.field("ux"), o.field("uy")
+    # x -> 31 - x maps the lattice onto itself about the disc centre 15.5
+    assert np.max(np.abs(ux + ux[:, ::-1])) < 1e-13
+    assert np.max(np.abs(uy - uy[:, ::-1])) < 1e-13
+    assert np.max(np.abs(uy)) > 1e-8
+
+
+# ------------------------------------------------------------------ P9
+def test_observable_formulas_against_tables_5_to_7():
+    """Eo (Eq. 40) and Re (Eq. 38) recomputed from Table 5 and the terminal
+    velocities of Table 7 (d = L/4 = 50) reproduce Table 6; the buoyancy drag of
+    Eq. 37 agrees with the Li correlation of Eq. 41 where Table 7 reports 0 error."""
+    t = _golden("paper_tables5to7_bubble.json")
+    rho_l, rho_g, d = 1.0, 1.0 / t["density_ratio"], t["d"]
+    for c in t["cases"]:
+        Eo = obs.eotvos(rho_l, rho_g, c["g"], d, c["sigma"])
+        assert abs(Eo - c["Eo"]) / c["Eo"] < 0.005
+        Re = obs.reynolds(rho_l, c["Ut_present"], d, c["n"], c["k"])
+        tol = 0.03 if c["case"] >= 4 else 0.10
+        assert abs(Re - c["Re"]) / c["Re"] < tol
+    c4 = t["cases"][3]
+    cd_buoy = obs.drag_coefficient(d, c4["g"], rho_l, rho_g, c4["Ut_present"])
+    Re4 = obs.reynolds(rho_l, c4["Ut_present"], d, c4["n"], c4["k"])
+    cd_li = obs.li_correlation(Re4, c4["n"], c4["E"])
+    assert abs(cd_buoy - cd_li) / cd_li < 0.05
+
+
+# ------------------------------------------------------------------ inputs
+def test_splitmix64_reference_vectors():
+    t = _golden("splitmix64_vectors.json")
+    for v in t["vectors"]:
+        got = inputs.splitmix64_at(v["seed"], np.arange(len(v["outputs"])))
+        assert [int(x) for x in got] == [int(h, 16) for h in v["outputs"]]
+
+
+def test_oracle_bubble_init_matches_input_generator():
+    p, b = inputs.small_case()
+    o = oracle.Oracle(p)
+    o.init_bubbles([list(x) for x in b], seed=5, noise=1e-8)
+    C = inputs.bubble_fields(p["nx"], p["ny"], 2, p["xi"], b, seed=5, noise=1e-8)
+    assert np.max(np.abs(o.field("C1") - C[0])) < 1e-15
+    # disc profile of Eq. 42 at the centre and one radius out
+    assert abs(C[0][32, 32] - (0.5 + 0.5 * math.tanh(-10 / 2.0))) < 2e-8
+    assert abs(C[0][32, 42] - 0.5) < 2e-8
