@@ -1,0 +1,301 @@
+"""Benchmark of the coupled power-law / Cahn-Hilliard D2Q9 step on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--nx NX]
+
+One step = one time step of the whole lattice (Sec. 2.2-2.3 of arXiv
+2207.09431: moments, chemical potentials, gradients, velocity and pressure,
+power-law relaxation time, collision of g and h, streaming with bounce-back).
+Workload: the rising-bubble set-up at 2048 x 4096 (R = 256, density ratio
+1000, n = 0.7, Eo = 10), synthetic and seeded.  The state (about 1.3 GB) is
+larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  Under torchrun every rank advances its own
+replica of the lattice (the method has no exchange between independent
+lattices), timing is the max over ranks and `value` the total over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2207_09431_gb300 import inputs  # noqa: E402
+
+METRIC = "coupled-step MLUPS (D2Q9, 2 components, FP32)"
+UNIT = "MLUPS"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for_smi(local, torch):
+    """nvidia-smi id of this process's GPU: its UUID when torch exposes it."""
+    try:
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[local] if vis else str(local)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# Algorithmic bytes per node of each kernel of the step (2 components, FP32):
+# every input plane read once and every output plane written once.
+def kernel_bytes_per_node(nh: int) -> dict:
+    f = 4
+    return {
+        "k_moments": f * (9 * nh + nh),
+        "k_fields": f * (nh + 9 + 1 + 3 + 3 + 1 + 1),
+        "k_sources": f * (nh + nh + nh),
+        "k_collide": f * (9 + nh + 3 + 1 + 2 + 1 + nh + 9 + 9 * nh),
+    }
+
+
+def step_bytes_per_node(nh: int) -> int:
+    """Algorithmic bytes of one time step: populations g (9), h (9 nh) and tau
+    read and written once."""
+    return 4 * 2 * (9 + 9 * nh + 1)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2207_09431_gb300 import lbm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p, bubbles = inputs.sweep_case(args.nx)
+    nx, ny = p["nx"], p["ny"]
+    nodes = nx * ny
+    nh = p["ncomp"] - 1
+    C = inputs.bubble_fields(nx, ny, 2, p["xi"], bubbles, seed=rank, noise=1e-8)
+    stream = torch.cuda.Stream(device=dev)
+    lat = lbm.Lattice(p, device=dev, stream=stream)
+    lat.set_fields(C)
+    lat.step(args.warmup)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(gpu_id_for_smi(local, torch))
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        lat.step(args.steps)
+        ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * nodes * args.steps / (ms_max * 1e-3) / 1e6
+
+    # dominant kernel: per-kernel device time measured by the library on this stream
+    kt = lat.kernel_times(reps=max(3, min(args.steps, 20)))
+    hbm, peak_kind = measured_peaks()
+    bpn = kernel_bytes_per_node(nh)
+    if kt:
+        dom = max(kt, key=kt.get)
+        achieved = bpn.get(dom, step_bytes_per_node(nh)) * nodes / (kt[dom] * 1e-3) / 1e9
+    else:
+        dom = "step"
+        achieved = step_bytes_per_node(nh) * nodes / (ms_max / args.steps * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "step_bytes_per_node": step_bytes_per_node(nh),
+                "step_frac": round(step_bytes_per_node(nh) * nodes / (ms_max / args.steps * 1e-3) / 1e9 / hbm, 4)}
+
+    # end to end through the C ABI with host buffers: upload the initial fields,
+    # advance K steps, read back the observables
+    e2e_lat = lat
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e2e_lat.set_fields(C)
+    e2e_lat.step(args.steps)
+    obs = e2e_lat.observables()
+    t1 = time.perf_counter()
+    h2d = 4 * nodes * (nh + 3)
+    d2h = 16 * 8 + 8 * 4 + 4 * args.steps * 0
+    e2e = {"value": round(nodes * args.steps / (t1 - t0) / 1e6, 1), "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "what": "lbm_set_fields from host doubles + lbm_step(K) + lbm_observables, wall clock"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded rising bubble)",
+        "config": {"workload": f"rising bubble {nx}x{ny}, R={nx // 8}, density ratio 1000, n=0.7, Eo=10, "
+                               "2 components, walls top/bottom",
+                   "nx": nx, "ny": ny, "nodes": nodes, "l2": "state 1.3 GB > L2 (no flush needed)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "e2e": e2e, "clocks": clk,
+        "gpu_launches": lat.launches_per_step() * args.steps,
+        "kernel_ms": {k: round(v, 5) for k, v in kt.items()},
+        "observables_after": {"rise_velocity": obs["rise_velocity"], "mass1": obs["mass"][0]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(target_s=15.0)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(target_s=15.0, nx=256):
+    """The FP64 oracle as it stands on one host core, on a bounded sample of the
+    workload: the same rising bubble at nx x 2nx for as many steps as fit in
+    about target_s seconds."""
+    import oracle
+
+    p, b = inputs.sweep_case(nx)
+    o = oracle.Oracle(p)
+    o.set_fields(inputs.bubble_fields(p["nx"], p["ny"], 2, p["xi"], b, seed=0, noise=1e-8))
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    steps = max(1, int(target_s / max(t1 - t0, 1e-6)))
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    mlups = p["nx"] * p["ny"] * steps / dt / 1e6
+    return {"value": round(mlups, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"rising bubble {p['nx']}x{p['ny']}, {steps} steps, FP64 C oracle, 1 thread"}
+
+
+def run_reference(args):
+    """The oracle timed as the reference arm, on the host cores, bounded per step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    nx = 256
+    p, b = inputs.sweep_case(nx)
+    o = oracle.Oracle(p)
+    o.set_fields(inputs.bubble_fields(p["nx"], p["ny"], 2, p["xi"], b, seed=0, noise=1e-8))
+    sub = 20  # lattice steps per bench step (bounded sample)
+    o.step(args.warmup * sub)
+    t0 = time.perf_counter()
+    o.step(args.steps * sub)
+    dt = time.perf_counter() - t0
+    nodes = p["nx"] * p["ny"]
+    value = nodes * args.steps * sub / dt / 1e6
+    sample = f"rising bubble {p['nx']}x{p['ny']} (same physics as the {args.nx}x{2 * args.nx} workload), {sub} lattice steps per step"
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded rising bubble)",
+            "impl": "reference",
+            "config": {"workload": f"rising bubble {nx}x{2 * nx}, R={nx // 8}, density ratio 1000, n=0.7, Eo=10"},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) coupled power-law / Cahn-Hilliard
+ * lattice Boltzmann step of arXiv 2207.09431 (Sec. 2).
+ *
+ * One handle = one D2Q9 lattice of nx x ny nodes with ncomp = 2 or 3
+ * components.  Component 1 is the (power-law) matrix liquid; with ncomp == 2
+ * only C1 is transported and the second phase is component 3 (C2 == 0); with
+ * ncomp == 3 C1 and C2 are transported and C3 = 1 - C1 - C2 (Eq. 1).
+ *
+ * Memory.  The library never allocates device memory for a lattice: the caller
+ * passes a device arena of at least lbm_required_bytes() bytes (for example a
+ * torch.uint8 tensor) and a CUDA stream, and keeps both alive until
+ * lbm_destroy().  All compute is enqueued on that stream.  The library never
+ * frees caller memory.
+ *
+ * Conventions.  Every call returns lbm_status.  On error the handle keeps its
+ * previous valid state and lbm_last_error() describes the failure.  A handle
+ * must not be used from two host threads at once.  Host-side inputs and
+ * outputs are double precision whatever the device storage.
+ *
+ * Device data layout (inside the arena): structure of arrays, one plane per
+ * population direction, planes of ny rows with a row pitch of nx rounded up to
+ * a multiple of 32 floats (128 bytes).  Node (x, y) of plane q is at
+ * q * plane + y * pitch + x.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_handle lbm_handle;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_E_INVAL = -1,    /* invalid argument or parameter set */
+  LBM_E_NOMEM = -2,    /* arena smaller than lbm_required_bytes() */
+  LBM_E_CUDA = -3,     /* a CUDA runtime call failed (message in lbm_last_error) */
+  LBM_E_DIVERGED = -4, /* a non-finite rho, p, u or tau appeared during lbm_step */
+  LBM_E_TIMEOUT = -5,  /* a bounded device wait ran out */
+  LBM_E_STATE = -6,    /* call out of order (e.g. lbm_step before initial fields) */
+  LBM_E_IO = -7        /* checkpoint file could not be read or written */
+} lbm_status;
+
+/* Problem statement of Sec. 2 (Eq. 1-33) plus the set-up of Sec. 3-4. */
+typedef struct {
+  int nx, ny;          /* lattice size, nx >= 1, ny >= 3 */
+  int ncomp;           /* 2 or 3 components (Eq. 1); ncomp - 1 order parameters transported */
+  int periodic_y;      /* 0: half-way bounce-back walls at y = -1/2 and ny - 1/2; 1: periodic */
+  double rho[3];       /* component densities rho_i */
+  double tau[3];       /* Newtonian relaxation times tau_i = nu_i / cs^2 (Eq. 14) */
+  int powerlaw;        /* 1: component 1 follows the truncated power law (Eq. 31, 33) */
+  double pl_n, pl_k;   /* power-law index n and consistency k (Eq. 31) */
+  double tau_min, tau_max; /* truncation of the power-law relaxation time (Eq. 33 on tau) */
+  double sigma12, sigma13, sigma23; /* pairwise surface tensions (Eq. 3) */
+  double Lambda;       /* total-spreading coefficient of Eq. 3 */
+  double xi;           /* interface width (Eq. 2) */
+  double D0;           /* mobility scale of Eq. 6 (the paper uses xi / 300) */
+  int mobility;        /* 0 constant, 1 variable mobility (Eq. 6) */
+  double gravity;      /* g of the body force F_b = -rho g j (Eq. 12) */
+  double force_x;      /* uniform body-force density along x (channel flows, Sec. 3.2-3.3) */
+  int fd_scheme;       /* directional derivatives: 0 central, 1 mixed central/biased */
+  int storage;         /* population storage: 0 FP32 (only FP32 is accepted) */
+  int gas_comp;        /* component whose moments lbm_observables reports (2 or 3) */
+} lbm_params;
+
+/* A disc of component `comp` (Eq. 42 profile). */
+typedef struct {
+  double cx, cy, r;
+  int comp;
+} lbm_bubble;
+
+/* Observables (Sec. 3.1 thresholded mass; Sec. 4.1-4.2 Eq. 37-40, 43-44). */
+typedef struct {
+  long long step;
+  double mass[3];          /* sum over nodes of C_i */
+  double mass_thr[3];      /* sum of C_i over nodes where C_i > 0.5 */
+  double area;             /* A = sum C_g (g = gas_comp) */
+  double centroid[2];      /* sum C_g x / A, sum C_g y / A (Eq. 44) */
+  double velocity[2];      /* sum C_g u / A (Eq. 43) */
+  double rise_velocity;    /* velocity[1] */
+  double y_integrated;     /* centroid y at the first call + trapezoidal time integral of rise_velocity */
+  double d_eq;             /* area-equivalent diameter 2 sqrt(A / pi) */
+  double aspect_E;         /* vertical / horizontal extent of C_g > 0.5 */
+  double drag_coefficient; /* Eq. 37 with U = rise_velocity */
+  double Re, Eo, Mo;       /* Eq. 38-40 with d = d_eq, U = rise_velocity */
+  double raw[15];          /* raw sums, layout of lbm_postprocess */
+} lbm_obs;
+
+/* Field ids for lbm_get_field.  Macroscopic fields are those of the current
+ * populations (Eq. 22-24); SHEAR is the strain rate of the last step (Eq. 25);
+ * SV the diffusion sources D lap(mu) + variable-mobility term of the last step. */
+enum {
+  LBM_FIELD_C1 = 0, LBM_FIELD_C2 = 1, LBM_FIELD_C3 = 2, LBM_FIELD_RHO = 3,
+  LBM_FIELD_P = 4, LBM_FIELD_UX = 5, LBM_FIELD_UY = 6, LBM_FIELD_TAU = 7,
+  LBM_FIELD_MU1 = 8, LBM_FIELD_MU2 = 9, LBM_FIELD_MU3 = 10,
+  LBM_FIELD_G = 11,      /* 9 planes of nx*ny, direction-major */
+  LBM_FIELD_H = 12,      /* (ncomp-1) x 9 planes */
+  LBM_FIELD_SHEAR = 13,
+  LBM_FIELD_SV = 16      /* (ncomp-1) planes */
+};
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int lbm_version(void);
+
+/* Bytes of device arena a lattice with these parameters needs; 0 if invalid. */
+size_t lbm_required_bytes(const lbm_params *p);
+
+/* Creates a handle.  dev_arena: device pointer, 256-byte aligned, at least
+ * lbm_required_bytes(p) bytes; cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream).  Validates the parameters (Sec. 2: Sigma_i > 0, xi > 0,
+ * positive densities, tau_min <= tau_max).  No state is valid until
+ * lbm_init_bubbles or lbm_set_fields. */
+lbm_status lbm_create(const lbm_params *p, void *dev_arena, size_t arena_bytes, void *cuda_stream,
+                      lbm_handle **out);
+
+/* Initial state from discs (Sec. 4.2, Eq. 42): each disc adds
+ * 0.5 - 0.5 tanh((r - R) / (xi / 2)) to its component (periodic distance along
+ * periodic axes), uniform noise in [-noise_amp, noise_amp] from SplitMix64 at
+ * counter (comp - 1) * nx * ny + node is added to every disc component, the
+ * matrix takes the rest; then as lbm_set_fields with p = u = 0.  Computed in
+ * FP64 on the host, uploaded, equilibria built on the device. */
+lbm_status lbm_init_bubbles(lbm_handle *h, const lbm_bubble *bubbles, int nb, unsigned long long seed,
+                            double noise_amp);
+
+/* Initial state from host fields (row-major ny x nx, double): C holds ncomp-1
+ * planes (C1, then C2); p, ux, uy may be NULL for zero.  Populations are the
+ * modified equilibria of Eq. 16 and Eq. 20; tau uses a zero strain rate. */
+lbm_status lbm_set_fields(lbm_handle *h, const double *C, const double *p, const double *ux,
+                          const double *uy);
+
+/* Enqueues nsteps time steps (Sec. 2.2-2.3) on the handle's stream and waits
+ * for them; returns LBM_E_DIVERGED if a non-finite value appeared. */
+lbm_status lbm_step(lbm_handle *h, long long nsteps);
+
+/* Computes the observables of the current state (FP64 sums on the device,
+ * post-processing on the host); synchronises the stream. */
+lbm_status lbm_observables(lbm_handle *h, lbm_obs *out);
+
+/* Copies field `field_id` (LBM_FIELD_*) to host_out as doubles; n is the
+ * capacity of host_out in values.  Synchronises the stream. */
+lbm_status lbm_get_field(lbm_handle *h, int field_id, double *host_out, size_t n);
+
+/* Checkpoint: header (magic, parameters, step) then populations and tau as
+ * stored.  lbm_load requires a handle created with identical parameters. */
+lbm_status lbm_save(lbm_handle *h, const char *path);
+lbm_status lbm_load(lbm_handle *h, const char *path);
+
+void lbm_destroy(lbm_handle *h);
+
+/* Measurement: number of kernels one lbm_step launches per time step, and
+ * their names. */
+int lbm_kernels_per_step(const lbm_handle *h);
+const char *lbm_kernel_name(const lbm_handle *h, int i);
+
+/* Measurement: advances nsteps time steps (they count as steps of the run)
+ * recording a CUDA event on the handle's stream around every kernel, and
+ * returns the mean device time of each kernel in ms_per_kernel[0..k-1],
+ * k = lbm_kernels_per_step(h) <= nkernels.  Synchronises the stream. */
+lbm_status lbm_profile_step(lbm_handle *h, long long nsteps, double *ms_per_kernel, int nkernels);
+
+/* Message of the last failure on this handle (empty if none). */
+const char *lbm_last_error(const lbm_handle *h);
+
+/* Host-only post-processing of 15 raw sums into observables (Eq. 37-40,
+ * 43-44).  raw = {M1, M2, M3, M1>, M2>, M3>, A, sum C_g x, sum C_g y,
+ * sum C_g ux, sum C_g uy, xmin, xmax, ymin, ymax}.  step and y_integrated are
+ * left at 0. */
+lbm_status lbm_postprocess(const lbm_params *p, const double raw[15], lbm_obs *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

@@ -1,0 +1,596 @@
+// Host side of the C ABI declared in include/lbm.h: parameter validation,
+// arena carving, initial conditions (Sec. 4.2, Eq. 42), the step loop, field
+// readback, observables post-processing (Sec. 4.1-4.2) and checkpoints.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_kernels.h"
+
+namespace {
+
+constexpr int kVersion = 100;  // 0.1.0
+constexpr size_t kAlign = 256;
+constexpr char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+
+// Number of FP32 planes the handle carves from the arena.
+struct Layout {
+  size_t plane_bytes;
+  size_t g, h, tau, C, mu, p, ux, uy, shear, SV, small, total;
+};
+
+Layout layout_of(const lbm_params &p) {
+  Layout L{};
+  const int nh = p.ncomp - 1;
+  L.plane_bytes = align_up((size_t)p.ny * pitch_of(p.nx) * sizeof(float), kAlign);
+  size_t off = 0;
+  auto take = [&](size_t planes) {
+    size_t o = off;
+    off += planes * L.plane_bytes;
+    return o;
+  };
+  L.g = take(2 * 9);
+  L.h = take(2 * 9 * (size_t)nh);
+  L.tau = take(2);
+  L.C = take(nh);
+  L.mu = take(3);
+  L.p = take(1);
+  L.ux = take(1);
+  L.uy = take(1);
+  L.shear = take(1);
+  L.SV = take(nh);
+  L.small = off;
+  off += align_up(16 * sizeof(double) + 8 * sizeof(int) + sizeof(unsigned), kAlign);
+  L.total = off;
+  return L;
+}
+
+const char *validate(const lbm_params *p) {
+  if (!p) return "params is NULL";
+  if (p->nx < 1 || p->ny < 3) return "need nx >= 1 and ny >= 3";
+  if ((long long)p->nx * p->ny > (1LL << 31)) return "lattice too large";
+  if (p->ncomp != 2 && p->ncomp != 3) return "ncomp must be 2 or 3";
+  if (p->fd_scheme != 0 && p->fd_scheme != 1) return "fd_scheme must be 0 or 1";
+  if (p->storage != 0) return "only FP32 storage (0) is supported";
+  if (p->mobility != 0 && p->mobility != 1) return "mobility must be 0 or 1";
+  if (p->gas_comp != 2 && p->gas_comp != 3) return "gas_comp must be 2 or 3";
+  if (p->ncomp == 2 && p->gas_comp != 3) return "with two components the gas is component 3";
+  for (int i = 0; i < 3; ++i)
+    if (!(p->rho[i] > 0) || !(p->tau[i] > 0)) return "densities and relaxation times must be positive";
+  const double S1 = p->sigma12 + p->sigma13 - p->sigma23;
+  const double S2 = p->sigma12 + p->sigma23 - p->sigma13;
+  const double S3 = p->sigma13 + p->sigma23 - p->sigma12;
+  if (!(S1 > 0 && S2 > 0 && S3 > 0)) return "capillary coefficients Sigma_i must be positive";
+  if (!(p->xi > 0)) return "interface width xi must be positive";
+  if (!(p->D0 >= 0)) return "D0 must be non-negative";
+  if (p->powerlaw && !(p->pl_k > 0 && p->pl_n > 0)) return "power law needs k > 0 and n > 0";
+  if (!(p->tau_min > 0 && p->tau_min <= p->tau_max)) return "need 0 < tau_min <= tau_max";
+  return nullptr;
+}
+
+lbm::DevParams dev_params(const lbm_params &p) {
+  lbm::DevParams d{};
+  d.nx = p.nx;
+  d.ny = p.ny;
+  d.pitch = pitch_of(p.nx);
+  d.ncomp = p.ncomp;
+  d.nh = p.ncomp - 1;
+  d.periodic_y = p.periodic_y ? 1 : 0;
+  d.powerlaw = p.powerlaw ? 1 : 0;
+  d.mobility = p.mobility;
+  d.fd_scheme = p.fd_scheme;
+  for (int i = 0; i < 3; ++i) {
+    d.rho[i] = (float)p.rho[i];
+    d.tau[i] = (float)p.tau[i];
+  }
+  d.pl_n = (float)p.pl_n;
+  d.pl_k = (float)p.pl_k;
+  d.tau_min = (float)p.tau_min;
+  d.tau_max = (float)p.tau_max;
+  d.sig12 = (float)p.sigma12;
+  d.sig13 = (float)p.sigma13;
+  d.sig23 = (float)p.sigma23;
+  d.Lambda = (float)p.Lambda;
+  // capillary coefficients and Sigma_T (Sec. 2.1), in double then rounded
+  const double S1 = p.sigma12 + p.sigma13 - p.sigma23;
+  const double S2 = p.sigma12 + p.sigma23 - p.sigma13;
+  const double S3 = p.sigma13 + p.sigma23 - p.sigma12;
+  d.Sig[0] = (float)S1;
+  d.Sig[1] = (float)S2;
+  d.Sig[2] = (float)S3;
+  d.SigT = (float)(3.0 / (1.0 / S1 + 1.0 / S2 + 1.0 / S3));
+  d.xi = (float)p.xi;
+  d.D0 = (float)p.D0;
+  d.gravity = (float)p.gravity;
+  d.force_x = (float)p.force_x;
+  d.plane = (long long)p.ny * d.pitch;
+  return d;
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014) at counter i: mix(seed + (i+1) gamma).
+uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct lbm_handle {
+  lbm_params prm;
+  lbm::DevParams dp;
+  Layout L;
+  cudaStream_t stream;
+  char *arena;
+  float *g[2], *h[2], *tau[2];
+  float *C, *mu, *p, *ux, *uy, *shear, *SV;
+  double *acc;
+  int *ext;
+  unsigned *err;
+  int cur;
+  bool initialized;
+  long long step;
+  bool have_prev;
+  long long prev_step;
+  double prev_v, y_int;
+  std::string last_error;
+  std::vector<float> stage;  // host staging (pitched FP32 planes)
+
+  lbm_status fail(lbm_status s, const std::string &msg) {
+    last_error = msg;
+    return s;
+  }
+  lbm_status cuda_fail(cudaError_t e, const char *where) {
+    last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return LBM_E_CUDA;
+  }
+  lbm::StepBuffers buffers(int in) const {
+    lbm::StepBuffers B{};
+    B.g_in = g[in];
+    B.h_in = h[in];
+    B.tau_in = tau[in];
+    B.g_out = g[1 - in];
+    B.h_out = h[1 - in];
+    B.tau_out = tau[1 - in];
+    B.C = C;
+    B.mu = mu;
+    B.p = p;
+    B.ux = ux;
+    B.uy = uy;
+    B.shear = shear;
+    B.SV = SV;
+    B.err = err;
+    return B;
+  }
+  size_t plane_floats() const { return (size_t)dp.plane; }
+};
+
+// Copies nplanes host planes (dense ny x nx doubles) into pitched device planes.
+static cudaError_t upload_planes(lbm_handle *h, float *dst, const double *src, int nplanes) {
+  const int nx = h->prm.nx, ny = h->prm.ny, pitch = h->dp.pitch;
+  h->stage.assign((size_t)nplanes * h->plane_floats(), 0.0f);
+  for (int q = 0; q < nplanes; ++q)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x)
+        h->stage[(size_t)q * h->plane_floats() + (size_t)y * pitch + x] =
+            src ? (float)src[((size_t)q * ny + y) * nx + x] : 0.0f;
+  for (int q = 0; q < nplanes; ++q) {
+    cudaError_t e = cudaMemcpyAsync(dst + (size_t)q * (h->L.plane_bytes / sizeof(float)),
+                                    h->stage.data() + (size_t)q * h->plane_floats(),
+                                    h->plane_floats() * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaStreamSynchronize(h->stream);
+}
+
+// Copies nplanes pitched device planes into dense host doubles.
+static cudaError_t download_planes(lbm_handle *h, const float *src, double *dst, int nplanes) {
+  const int nx = h->prm.nx, ny = h->prm.ny, pitch = h->dp.pitch;
+  h->stage.assign((size_t)nplanes * h->plane_floats(), 0.0f);
+  for (int q = 0; q < nplanes; ++q) {
+    cudaError_t e = cudaMemcpyAsync(h->stage.data() + (size_t)q * h->plane_floats(),
+                                    src + (size_t)q * (h->L.plane_bytes / sizeof(float)),
+                                    h->plane_floats() * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return e;
+  for (int q = 0; q < nplanes; ++q)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x)
+        dst[((size_t)q * ny + y) * nx + x] = h->stage[(size_t)q * h->plane_floats() + (size_t)y * pitch + x];
+  return cudaSuccess;
+}
+
+extern "C" {
+
+int lbm_version(void) { return kVersion; }
+
+size_t lbm_required_bytes(const lbm_params *p) {
+  if (validate(p)) return 0;
+  return layout_of(*p).total;
+}
+
+lbm_status lbm_create(const lbm_params *p, void *dev_arena, size_t arena_bytes, void *cuda_stream,
+                      lbm_handle **out) {
+  if (!out) return LBM_E_INVAL;
+  *out = nullptr;
+  if (validate(p)) return LBM_E_INVAL;
+  if (!dev_arena || ((uintptr_t)dev_arena % kAlign) != 0) return LBM_E_INVAL;
+  Layout L = layout_of(*p);
+  if (arena_bytes < L.total) return LBM_E_NOMEM;
+  lbm_handle *h = new (std::nothrow) lbm_handle();
+  if (!h) return LBM_E_NOMEM;
+  h->prm = *p;
+  h->dp = dev_params(*p);
+  h->L = L;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->arena = (char *)dev_arena;
+  const size_t pf = L.plane_bytes / sizeof(float);
+  const int nh = p->ncomp - 1;
+  for (int b = 0; b < 2; ++b) {
+    h->g[b] = (float *)(h->arena + L.g) + (size_t)b * 9 * pf;
+    h->h[b] = (float *)(h->arena + L.h) + (size_t)b * 9 * nh * pf;
+    h->tau[b] = (float *)(h->arena + L.tau) + (size_t)b * pf;
+  }
+  h->C = (float *)(h->arena + L.C);
+  h->mu = (float *)(h->arena + L.mu);
+  h->p = (float *)(h->arena + L.p);
+  h->ux = (float *)(h->arena + L.ux);
+  h->uy = (float *)(h->arena + L.uy);
+  h->shear = (float *)(h->arena + L.shear);
+  h->SV = (float *)(h->arena + L.SV);
+  h->acc = (double *)(h->arena + L.small);
+  h->ext = (int *)(h->acc + 16);
+  h->err = (unsigned *)(h->ext + 8);
+  // plane stride used by the kernels must match the arena planes
+  h->dp.plane = (long long)pf;
+  h->cur = 0;
+  h->initialized = false;
+  h->step = 0;
+  h->have_prev = false;
+  cudaError_t e = cudaMemsetAsync(h->arena, 0, L.total, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    delete h;
+    return LBM_E_CUDA;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_fields(lbm_handle *h, const double *C, const double *p, const double *ux, const double *uy) {
+  if (!h) return LBM_E_INVAL;
+  if (!C) return h->fail(LBM_E_INVAL, "C is NULL");
+  const int nh = h->prm.ncomp - 1;
+  cudaError_t e = upload_planes(h, h->C, C, nh);
+  if (e == cudaSuccess) e = upload_planes(h, h->p, p, 1);
+  if (e == cudaSuccess) e = upload_planes(h, h->ux, ux, 1);
+  if (e == cudaSuccess) e = upload_planes(h, h->uy, uy, 1);
+  if (e != cudaSuccess) return h->cuda_fail(e, "lbm_set_fields upload");
+  // equilibria into buffer 0
+  lbm::StepBuffers B = h->buffers(1);  // *_out of buffer index 1 is buffer 0
+  lbm::launch_init(h->dp, B, h->stream);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "lbm_set_fields init kernel");
+  h->cur = 0;
+  h->initialized = true;
+  h->step = 0;
+  h->have_prev = false;
+  h->last_error.clear();
+  return LBM_OK;
+}
+
+lbm_status lbm_init_bubbles(lbm_handle *h, const lbm_bubble *bubbles, int nb, unsigned long long seed,
+                            double noise_amp) {
+  if (!h) return LBM_E_INVAL;
+  if (nb < 0 || (nb > 0 && !bubbles)) return h->fail(LBM_E_INVAL, "bad bubble list");
+  const int nx = h->prm.nx, ny = h->prm.ny, nh = h->prm.ncomp - 1;
+  const size_t n = (size_t)nx * ny;
+  std::vector<double> comp[2] = {std::vector<double>(n, 0.0), std::vector<double>(n, 0.0)};  // comps 2, 3
+  bool used[2] = {false, false};
+  for (int b = 0; b < nb; ++b) {
+    const int c = bubbles[b].comp;
+    if (c < 2 || c > 3 || (nh == 1 && c != 3)) return h->fail(LBM_E_INVAL, "disc component must be 3 (or 2 with ncomp 3)");
+    used[c - 2] = true;
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        double dx = std::fabs(x - bubbles[b].cx), dy = std::fabs(y - bubbles[b].cy);
+        if (dx > 0.5 * nx) dx = nx - dx;
+        if (h->prm.periodic_y && dy > 0.5 * ny) dy = ny - dy;
+        const double r = std::sqrt(dx * dx + dy * dy);
+        comp[c - 2][(size_t)y * nx + x] += 0.5 - 0.5 * std::tanh((r - bubbles[b].r) / (0.5 * h->prm.xi));
+      }
+  }
+  for (int c = 0; c < 2; ++c) {
+    if (!used[c] || noise_amp == 0.0) continue;
+    for (size_t k = 0; k < n; ++k) {
+      const uint64_t z = splitmix64_at(seed, (uint64_t)(c + 1) * n + k);
+      const double u01 = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+      comp[c][k] += noise_amp * (2.0 * u01 - 1.0);
+    }
+  }
+  std::vector<double> Cin((size_t)nh * n);
+  for (size_t k = 0; k < n; ++k) {
+    Cin[k] = 1.0 - comp[0][k] - comp[1][k];
+    if (nh == 2) Cin[n + k] = comp[0][k];
+  }
+  return lbm_set_fields(h, Cin.data(), nullptr, nullptr, nullptr);
+}
+
+lbm_status lbm_step(lbm_handle *h, long long nsteps) {
+  if (!h) return LBM_E_INVAL;
+  if (!h->initialized) return h->fail(LBM_E_STATE, "lbm_step before initial fields");
+  if (nsteps < 0) return h->fail(LBM_E_INVAL, "nsteps < 0");
+  cudaError_t e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "lbm_step memset");
+  for (long long t = 0; t < nsteps; ++t) {
+    lbm::launch_split_step(h->dp, h->buffers(h->cur), h->stream);
+    h->cur = 1 - h->cur;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return h->cuda_fail(e, "lbm_step launch");
+  unsigned flag = 0;
+  e = cudaMemcpyAsync(&flag, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "lbm_step");
+  h->step += nsteps;
+  if (flag) return h->fail(LBM_E_DIVERGED, "non-finite rho, p, u or tau during lbm_step");
+  return LBM_OK;
+}
+
+static lbm_status compute_macros(lbm_handle *h) {
+  lbm::launch_macros(h->dp, h->buffers(h->cur), h->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return h->cuda_fail(e, "macro kernels");
+  return LBM_OK;
+}
+
+lbm_status lbm_postprocess(const lbm_params *p, const double raw[15], lbm_obs *o) {
+  if (!p || !raw || !o) return LBM_E_INVAL;
+  std::memset(o, 0, sizeof(*o));
+  for (int i = 0; i < 15; ++i) o->raw[i] = raw[i];
+  for (int i = 0; i < 3; ++i) {
+    o->mass[i] = raw[i];
+    o->mass_thr[i] = raw[3 + i];
+  }
+  const int gc = (p->gas_comp == 2 || p->gas_comp == 3) ? p->gas_comp : 3;
+  const double rho_l = p->rho[0], rho_g = p->rho[gc - 1];
+  const double sigma = gc == 3 ? p->sigma13 : p->sigma12;
+  const double g = p->gravity;
+  const double n = p->powerlaw ? p->pl_n : 1.0;
+  const double k = p->powerlaw ? p->pl_k : rho_l * p->tau[0] / 3.0;
+  const double A = raw[6];
+  const double nan = std::nan("");
+  o->area = A;
+  if (A > 0) {
+    o->centroid[0] = raw[7] / A;  // Eq. 44
+    o->centroid[1] = raw[8] / A;
+    o->velocity[0] = raw[9] / A;  // Eq. 43
+    o->velocity[1] = raw[10] / A;
+  } else {
+    o->centroid[0] = o->centroid[1] = o->velocity[0] = o->velocity[1] = nan;
+  }
+  const double U = o->velocity[1];
+  o->rise_velocity = U;
+  const double d = A > 0 ? 2.0 * std::sqrt(A / M_PI) : nan;  // area-equivalent diameter
+  o->d_eq = d;
+  o->aspect_E = raw[11] >= 0 ? (raw[14] - raw[13] + 1.0) / (raw[12] - raw[11] + 1.0) : nan;
+  o->drag_coefficient = (A > 0 && U != 0 && g != 0) ? 4.0 * d * g * (rho_l - rho_g) / (3.0 * rho_l * U * U) : nan;
+  o->Re = A > 0 ? rho_l * std::pow(std::fabs(U), 2.0 - n) * std::pow(d, n) / k : nan;  // Eq. 38
+  o->Eo = A > 0 ? (rho_l - rho_g) * g * d * d / sigma : nan;                             // Eq. 40
+  o->Mo = (A > 0 && U != 0)
+              ? g * (rho_l - rho_g) / (rho_l * rho_l * sigma * sigma * sigma) *
+                    std::pow(k * std::pow(std::fabs(U) / d, n - 1.0), 4.0)
+              : nan;  // Eq. 39
+  return LBM_OK;
+}
+
+lbm_status lbm_observables(lbm_handle *h, lbm_obs *out) {
+  if (!h || !out) return LBM_E_INVAL;
+  if (!h->initialized) return h->fail(LBM_E_STATE, "observables before initial fields");
+  lbm_status st = compute_macros(h);
+  if (st != LBM_OK) return st;
+  cudaError_t e = cudaMemsetAsync(h->acc, 0, 16 * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ext, 0x7f, 8 * sizeof(int), h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "observables memset");
+  lbm::launch_observables(h->dp, h->buffers(h->cur), h->prm.gas_comp, h->acc, h->ext, h->stream);
+  double acc[16];
+  int ext[8];
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, h->acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ext, h->ext, sizeof(ext), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "observables");
+  double raw[15];
+  for (int i = 0; i < 11; ++i) raw[i] = acc[i];
+  const bool any = ext[0] != 0x7f7f7f7f;
+  raw[11] = any ? ext[0] : -1.0;
+  raw[12] = any ? -ext[1] : -1.0;
+  raw[13] = any ? ext[2] : -1.0;
+  raw[14] = any ? -ext[3] : -1.0;
+  lbm_postprocess(&h->prm, raw, out);
+  out->step = h->step;
+  // centroid y at the first call plus the trapezoidal integral of the rise velocity
+  if (!h->have_prev) {
+    h->y_int = out->centroid[1];
+    h->have_prev = true;
+  } else {
+    h->y_int += 0.5 * (h->prev_v + out->rise_velocity) * (double)(h->step - h->prev_step);
+  }
+  h->prev_step = h->step;
+  h->prev_v = out->rise_velocity;
+  out->y_integrated = h->y_int;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_field(lbm_handle *h, int id, double *out, size_t n) {
+  if (!h || !out) return LBM_E_INVAL;
+  if (!h->initialized) return h->fail(LBM_E_STATE, "get_field before initial fields");
+  const int nh = h->prm.ncomp - 1;
+  const size_t N = (size_t)h->prm.nx * h->prm.ny;
+  size_t need;
+  switch (id) {
+    case LBM_FIELD_G: need = 9 * N; break;
+    case LBM_FIELD_H: need = (size_t)9 * nh * N; break;
+    case LBM_FIELD_SV: need = (size_t)nh * N; break;
+    case LBM_FIELD_C1: case LBM_FIELD_C2: case LBM_FIELD_C3: case LBM_FIELD_RHO: case LBM_FIELD_P:
+    case LBM_FIELD_UX: case LBM_FIELD_UY: case LBM_FIELD_TAU: case LBM_FIELD_MU1: case LBM_FIELD_MU2:
+    case LBM_FIELD_MU3: case LBM_FIELD_SHEAR: need = N; break;
+    default: return h->fail(LBM_E_INVAL, "unknown field id");
+  }
+  if (n < need) return h->fail(LBM_E_INVAL, "output buffer too small");
+  const size_t pf = h->L.plane_bytes / sizeof(float);
+  cudaError_t e = cudaSuccess;
+  switch (id) {
+    case LBM_FIELD_G: e = download_planes(h, h->g[h->cur], out, 9); break;
+    case LBM_FIELD_H: e = download_planes(h, h->h[h->cur], out, 9 * nh); break;
+    case LBM_FIELD_TAU: e = download_planes(h, h->tau[h->cur], out, 1); break;
+    case LBM_FIELD_SHEAR: e = download_planes(h, h->shear, out, 1); break;
+    case LBM_FIELD_SV: e = download_planes(h, h->SV, out, nh); break;
+    default: {
+      lbm_status st = compute_macros(h);
+      if (st != LBM_OK) return st;
+      if (id == LBM_FIELD_C1) e = download_planes(h, h->C, out, 1);
+      else if (id == LBM_FIELD_C2) {
+        if (nh == 2) e = download_planes(h, h->C + pf, out, 1);
+        else std::memset(out, 0, N * sizeof(double));
+      } else if (id == LBM_FIELD_C3 || id == LBM_FIELD_RHO) {
+        std::vector<double> c(2 * N, 0.0);
+        e = download_planes(h, h->C, c.data(), nh);
+        if (e == cudaSuccess)
+          for (size_t k = 0; k < N; ++k) {
+            // C3 = 1 - C1 - C2 (Eq. 1); rho by the clipped mixture law (R1)
+            const double C1 = (float)c[k], C2 = nh == 2 ? (float)c[N + k] : 0.0;
+            const double C3 = (double)(1.0f - (float)C1 - (float)C2);
+            if (id == LBM_FIELD_C3) {
+              out[k] = C3;
+            } else {
+              double w[3] = {C1, C2, C3}, s = 0;
+              for (double &v : w) { v = v < 0 ? 0 : (v > 1 ? 1 : v); s += v; }
+              out[k] = (w[0] * h->prm.rho[0] + w[1] * h->prm.rho[1] + w[2] * h->prm.rho[2]) / s;
+            }
+          }
+      } else if (id == LBM_FIELD_P) e = download_planes(h, h->p, out, 1);
+      else if (id == LBM_FIELD_UX) e = download_planes(h, h->ux, out, 1);
+      else if (id == LBM_FIELD_UY) e = download_planes(h, h->uy, out, 1);
+      else e = download_planes(h, h->mu + (size_t)(id - LBM_FIELD_MU1) * pf, out, 1);
+    }
+  }
+  if (e != cudaSuccess) return h->cuda_fail(e, "lbm_get_field");
+  return LBM_OK;
+}
+
+lbm_status lbm_save(lbm_handle *h, const char *path) {
+  if (!h || !path) return LBM_E_INVAL;
+  if (!h->initialized) return h->fail(LBM_E_STATE, "save before initial fields");
+  const int nh = h->prm.ncomp - 1;
+  const size_t pf = h->L.plane_bytes / sizeof(float);
+  const int nplanes = 9 + 9 * nh + 1;
+  std::vector<float> buf((size_t)nplanes * pf);
+  cudaError_t e = cudaMemcpyAsync(buf.data(), h->g[h->cur], 9 * pf * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(buf.data() + 9 * pf, h->h[h->cur], 9 * nh * pf * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(buf.data() + (size_t)(9 + 9 * nh) * pf, h->tau[h->cur], pf * sizeof(float),
+                        cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "lbm_save");
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return h->fail(LBM_E_IO, std::string("cannot open ") + path);
+  long long hdr[2] = {h->step, (long long)buf.size()};
+  bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(&h->prm, sizeof(lbm_params), 1, f) == 1 &&
+            std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return h->fail(LBM_E_IO, "short write");
+  return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_handle *h, const char *path) {
+  if (!h || !path) return LBM_E_INVAL;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return h->fail(LBM_E_IO, std::string("cannot open ") + path);
+  char magic[8];
+  lbm_params prm;
+  long long hdr[2];
+  const int nh = h->prm.ncomp - 1;
+  const size_t pf = h->L.plane_bytes / sizeof(float);
+  const size_t count = (size_t)(9 + 9 * nh + 1) * pf;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+            std::fread(&prm, sizeof(prm), 1, f) == 1 && std::fread(hdr, sizeof(hdr), 1, f) == 1;
+  if (ok && (std::memcmp(&prm, &h->prm, sizeof(prm)) != 0 || hdr[1] != (long long)count)) {
+    std::fclose(f);
+    return h->fail(LBM_E_INVAL, "checkpoint parameters differ from the handle's");
+  }
+  std::vector<float> buf(count);
+  ok = ok && std::fread(buf.data(), sizeof(float), count, f) == count;
+  std::fclose(f);
+  if (!ok) return h->fail(LBM_E_IO, "truncated or foreign checkpoint");
+  cudaError_t e = cudaMemcpyAsync(h->g[0], buf.data(), 9 * pf * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h[0], buf.data() + 9 * pf, 9 * nh * pf * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->tau[0], buf.data() + (size_t)(9 + 9 * nh) * pf, pf * sizeof(float),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return h->cuda_fail(e, "lbm_load");
+  h->cur = 0;
+  h->step = hdr[0];
+  h->initialized = true;
+  h->have_prev = false;
+  return LBM_OK;
+}
+
+int lbm_kernels_per_step(const lbm_handle *h) { return h ? lbm::kSplitKernels : 0; }
+
+const char *lbm_kernel_name(const lbm_handle *h, int i) {
+  static const char *names[lbm::kSplitKernels] = {"k_moments", "k_fields", "k_sources", "k_collide"};
+  if (!h || i < 0 || i >= lbm::kSplitKernels) return "";
+  return names[i];
+}
+
+lbm_status lbm_profile_step(lbm_handle *h, long long nsteps, double *ms_per_kernel, int nkernels) {
+  if (!h || !ms_per_kernel || nsteps < 1) return LBM_E_INVAL;
+  if (!h->initialized) return h->fail(LBM_E_STATE, "profile before initial fields");
+  const int K = lbm::kSplitKernels;
+  if (nkernels < K) return h->fail(LBM_E_INVAL, "ms_per_kernel too small");
+  std::vector<cudaEvent_t> ev((size_t)(K + 1) * nsteps);
+  for (auto &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return h->fail(LBM_E_CUDA, "cudaEventCreate");
+  for (long long t = 0; t < nsteps; ++t) {
+    lbm::launch_split_step(h->dp, h->buffers(h->cur), h->stream, ev.data() + t * (K + 1));
+    h->cur = 1 - h->cur;
+  }
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  for (int i = 0; i < K; ++i) ms_per_kernel[i] = 0.0;
+  for (long long t = 0; t < nsteps && e == cudaSuccess; ++t)
+    for (int i = 0; i < K; ++i) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[t * (K + 1) + i], ev[t * (K + 1) + i + 1]);
+      ms_per_kernel[i] += ms / (double)nsteps;
+    }
+  for (auto &x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return h->cuda_fail(e, "lbm_profile_step");
+  h->step += nsteps;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_handle *h) { delete h; }
+
+const char *lbm_last_error(const lbm_handle *h) { return h ? h->last_error.c_str() : "NULL handle"; }
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Device-side definitions of the coupled power-law / Cahn-Hilliard D2Q9 step
+// (arXiv 2207.09431, Sec. 2).  FP32 arithmetic throughout.
+//
+// Readings of the paper applied here (the same ones the CPU oracle applies):
+//  R1  mixture laws rho = sum c_i rho_i, tau = sum c_i tau_i with weights
+//      c_i = clip(C_i, 0, 1) / sum_j clip(C_j, 0, 1) (Sec. 2.2 names no law);
+//  R2  isotropic gradient 3 sum w e X(x+e), Laplacian 6 sum w (X(x+e) - X(x));
+//      (e_a - u).grad X = directional derivative along e_a - u . isotropic;
+//  R3  p = sum g + (1/2) cs^2 u . grad rho (Eq. 24 with the half restored);
+//  R4  tau_PL = eta / (rho cs^2) clamped to [tau_min, tau_max], node tau =
+//      sum c_i tau_i with tau_1 = tau_PL, strain rate from the previous tau;
+//  R8  variable-mobility term (D0/Sigma_i)(1 - 2 C_i) grad C_i . grad mu_i;
+//  R9  destination-side source terms of Eq. 18 at the arrival node;
+//  R10 half-way walls, ghost rows mirror the fluid rows;
+//  R23 strain rate D = -Pi / (2 tau rho cs^2) with Pi from Eq. 29.
+#pragma once
+
+#include <cstdint>
+
+#include "lbm_devparams.h"
+
+namespace lbm {
+
+// D2Q9 (Eq. 10-11): 0 rest, 1-4 E N W S, 5-8 NE NW SW SE.
+static __device__ __constant__ int c_ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static __device__ __constant__ int c_ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static __device__ __constant__ float c_w[9] = {4.f / 9.f,  1.f / 9.f,  1.f / 9.f,  1.f / 9.f, 1.f / 9.f,
+                                        1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
+static __device__ __constant__ int c_opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+constexpr float kCs2 = 1.0f / 3.0f;
+
+// Periodic wrap along x for |dx| <= nx.
+__device__ __forceinline__ int wrap_x(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
+
+// y index of the value seen at row y (periodic, or the mirror ghost rows of R10)
+// for |offset| <= ny.
+__device__ __forceinline__ int wrap_y(int y, int ny, int periodic) {
+  if (periodic) return y < 0 ? y + ny : (y >= ny ? y - ny : y);
+  return y < 0 ? -1 - y : (y >= ny ? 2 * ny - 1 - y : y);
+}
+
+// Gamma_a(u) = f_a^eq / rho (Eq. 9).
+__device__ __forceinline__ float gamma_a(int a, float ux, float uy) {
+  float eu = c_ex[a] * ux + c_ey[a] * uy;
+  float uu = ux * ux + uy * uy;
+  return c_w[a] * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
+}
+
+// Mixture weights of reading R1.
+__device__ __forceinline__ void mixture_weights(float C1, float C2, float C3, float c[3]) {
+  c[0] = fminf(fmaxf(C1, 0.0f), 1.0f);
+  c[1] = fminf(fmaxf(C2, 0.0f), 1.0f);
+  c[2] = fminf(fmaxf(C3, 0.0f), 1.0f);
+  float inv = 1.0f / (c[0] + c[1] + c[2]);
+  c[0] *= inv;
+  c[1] *= inv;
+  c[2] *= inv;
+}
+
+__device__ __forceinline__ float rho_of(const DevParams &P, float C1, float C2, float C3) {
+  float c[3];
+  mixture_weights(C1, C2, C3, c);
+  return c[0] * P.rho[0] + c[1] * P.rho[1] + c[2] * P.rho[2];
+}
+
+// Chemical potentials mu_1..3 (Eq. 5) from C and its isotropic Laplacian.
+__device__ __forceinline__ void chem_potentials(const DevParams &P, const float C[3], const float lapC[3],
+                                                float mu[3]) {
+  const float C1 = C[0], C2 = C[1], C3 = C[2];
+  const float S1 = P.Sig[0], S2 = P.Sig[1], S3 = P.Sig[2];
+  const float mix = S1 * C1 + S2 * C2 + S3 * C3;
+  const float L = P.Lambda;
+  // partial derivatives of E0 (Eq. 3)
+  float d0 = 2.f * P.sig12 * C1 * C2 * C2 + 2.f * P.sig13 * C1 * C3 * C3 + C2 * C3 * (mix + S1 * C1) +
+             2.f * L * C1 * C2 * C2 * C3 * C3;
+  float d1 = 2.f * P.sig12 * C1 * C1 * C2 + 2.f * P.sig23 * C2 * C3 * C3 + C1 * C3 * (mix + S2 * C2) +
+             2.f * L * C1 * C1 * C2 * C3 * C3;
+  float d2 = 2.f * P.sig13 * C1 * C1 * C3 + 2.f * P.sig23 * C2 * C2 * C3 + C1 * C2 * (mix + S3 * C3) +
+             2.f * L * C1 * C1 * C2 * C2 * C3;
+  const float pre = 4.f * P.SigT / P.xi;
+  mu[0] = pre * ((d0 - d1) / S2 + (d0 - d2) / S3) - 0.75f * P.xi * S1 * lapC[0];
+  mu[1] = pre * ((d1 - d0) / S1 + (d1 - d2) / S3) - 0.75f * P.xi * S2 * lapC[1];
+  mu[2] = pre * ((d2 - d0) / S1 + (d2 - d1) / S2) - 0.75f * P.xi * S3 * lapC[2];
+}
+
+// Power-law relaxation time at strain rate gd (Eq. 31-33, reading R4).
+__device__ __forceinline__ float tau_powerlaw(const DevParams &P, float gd, float rho) {
+  float eta = P.pl_k * powf(gd, P.pl_n - 1.0f);
+  float t = eta / (rho * kCs2);
+  t = (t <= P.tau_max) ? t : P.tau_max;  // also maps +inf (gd == 0, n < 1) to tau_max
+  return fmaxf(t, P.tau_min);
+}
+
+__device__ __forceinline__ float tau_mix(const DevParams &P, float C1, float C2, float C3, float tau1) {
+  float c[3];
+  mixture_weights(C1, C2, C3, c);
+  return c[0] * tau1 + c[1] * P.tau[1] + c[2] * P.tau[2];
+}
+
+}  // namespace lbm

@@ -1,0 +1,28 @@
+// Launchers shared between the C-ABI host code and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_devparams.h"
+
+namespace lbm {
+
+// Device buffers of one step.  *_in are the current state, *_out the next one;
+// the remaining planes are scratch fields.
+struct StepBuffers {
+  const float *g_in, *h_in, *tau_in;
+  float *g_out, *h_out, *tau_out;
+  float *C, *mu, *p, *ux, *uy, *shear, *SV;
+  unsigned *err;
+};
+
+// Launches one step; if ev is non-null, records ev[i] before kernel i and
+// ev[nkernels] after the last one.
+constexpr int kSplitKernels = 4;
+void launch_split_step(const DevParams &P, const StepBuffers &B, cudaStream_t s, cudaEvent_t *ev = nullptr);
+void launch_macros(const DevParams &P, const StepBuffers &B, cudaStream_t s);
+void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s);
+void launch_observables(const DevParams &P, const StepBuffers &B, int gas_comp, double *acc, int *ext,
+                        cudaStream_t s);
+
+}  // namespace lbm

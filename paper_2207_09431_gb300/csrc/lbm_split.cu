@@ -1,0 +1,433 @@
+// Multi-pass form of the coupled D2Q9 step (arXiv 2207.09431, Sec. 2.2-2.3):
+//   k_moments  C_i = sum_a h_a^i                         (Eq. 22)
+//   k_fields   rho, mu (Eq. 5), u (Eq. 23), p (Eq. 24/R3), new tau (Eq. 25-33)
+//   k_sources  S_i + V_i = D_i lap(mu_i) + variable-mobility term (Eq. 6, 21)
+//   k_collide  collision of g (Eq. 14) and h (Eq. 18), pushed to the
+//              neighbours with half-way bounce-back and the destination-side
+//              source term (R9)
+// The intermediate fields live in scratch planes carved from the caller's
+// arena.  One thread per node; all arithmetic FP32.
+#include "lbm_device.cuh"
+#include "lbm_kernels.h"
+
+namespace lbm {
+
+namespace {
+
+// Order parameter j (0..2) at node (x, y) of the scratch planes (C3 derived).
+struct CReader {
+  const float *C;
+  long long plane;
+  int nh;
+  __device__ __forceinline__ void at(long long k, float out[3]) const {
+    out[0] = C[k];
+    out[1] = (nh == 2) ? C[plane + k] : 0.0f;
+    out[2] = 1.0f - out[0] - out[1];
+  }
+};
+
+__device__ __forceinline__ long long node_index(const DevParams &P, int x, int y) {
+  return (long long)y * P.pitch + x;
+}
+
+__device__ __forceinline__ long long shifted(const DevParams &P, int x, int y, int dx, int dy) {
+  return node_index(P, wrap_x(x + dx, P.nx), wrap_y(y + dy, P.ny, P.periodic_y));
+}
+
+// Directional derivative e_a . grad X from samples X(x - e), X(x), X(x + e),
+// X(x + 2e) (R2; mixed = mean of central and second-order biased forms).
+__device__ __forceinline__ float dir_deriv(int scheme, float xm, float x0, float xp, float xpp) {
+  if (scheme == 0) return 0.5f * (xp - xm);
+  return 0.25f * (-xpp + 5.0f * xp - 3.0f * x0 - xm);
+}
+
+// Everything the forcing terms need at one node.
+struct NodeCtx {
+  float C[3], rho, ux, uy, p, mu[3];
+  float gC[3][2], grho[2], gp[2], Fs[2], Fb[2];
+  float dC[3][9], drho[9], dp[9];
+};
+
+// Gathers C (radius 1 or 2), rho (from C), p (radius 1 or 2) around (x, y).
+__device__ void gather_gradients(const DevParams &P, const CReader &cr, const float *pf, int x, int y,
+                                 NodeCtx &n) {
+  const long long k0 = node_index(P, x, y);
+  float Cn[9][3], rn[9], pn[9];
+  for (int a = 0; a < 9; ++a) {
+    long long k = shifted(P, x, y, c_ex[a], c_ey[a]);
+    cr.at(k, Cn[a]);
+    rn[a] = rho_of(P, Cn[a][0], Cn[a][1], Cn[a][2]);
+    pn[a] = pf[k];
+  }
+  (void)k0;
+  for (int j = 0; j < 3; ++j) {
+    n.C[j] = Cn[0][j];
+    float sx = 0.f, sy = 0.f;
+    for (int a = 0; a < 9; ++a) {
+      sx += c_w[a] * c_ex[a] * Cn[a][j];
+      sy += c_w[a] * c_ey[a] * Cn[a][j];
+    }
+    n.gC[j][0] = 3.0f * sx;
+    n.gC[j][1] = 3.0f * sy;
+  }
+  n.rho = rn[0];
+  n.p = pn[0];
+  {
+    float sx = 0.f, sy = 0.f, qx = 0.f, qy = 0.f;
+    for (int a = 0; a < 9; ++a) {
+      sx += c_w[a] * c_ex[a] * rn[a];
+      sy += c_w[a] * c_ey[a] * rn[a];
+      qx += c_w[a] * c_ex[a] * pn[a];
+      qy += c_w[a] * c_ey[a] * pn[a];
+    }
+    n.grho[0] = 3.0f * sx;
+    n.grho[1] = 3.0f * sy;
+    n.gp[0] = 3.0f * qx;
+    n.gp[1] = 3.0f * qy;
+  }
+  for (int a = 0; a < 9; ++a) {
+    const int o = c_opp[a];
+    float C2e[3] = {0.f, 0.f, 0.f}, r2e = 0.f, p2e = 0.f;
+    if (P.fd_scheme == 1) {
+      long long k2 = shifted(P, x, y, 2 * c_ex[a], 2 * c_ey[a]);
+      cr.at(k2, C2e);
+      r2e = rho_of(P, C2e[0], C2e[1], C2e[2]);
+      p2e = pf[k2];
+    }
+    for (int j = 0; j < 3; ++j) n.dC[j][a] = dir_deriv(P.fd_scheme, Cn[o][j], Cn[0][j], Cn[a][j], C2e[j]);
+    n.drho[a] = dir_deriv(P.fd_scheme, rn[o], rn[0], rn[a], r2e);
+    n.dp[a] = dir_deriv(P.fd_scheme, pn[o], pn[0], pn[a], p2e);
+  }
+}
+
+// Forcing of Eq. 14 for direction a.
+__device__ __forceinline__ float phi_g(const NodeCtx &n, int a, float G) {
+  float e_rho = n.drho[a] - (n.ux * n.grho[0] + n.uy * n.grho[1]);
+  float e_Fs = n.mu[0] * n.dC[0][a] + n.mu[1] * n.dC[1][a] + n.mu[2] * n.dC[2][a] -
+               (n.ux * n.Fs[0] + n.uy * n.Fs[1]);
+  float e_Fb = (c_ex[a] - n.ux) * n.Fb[0] + (c_ey[a] - n.uy) * n.Fb[1];
+  return e_rho * kCs2 * (G - c_w[a]) + (e_Fs + e_Fb) * G;
+}
+
+// Forcing of Eq. 18 for order parameter i, direction a.
+__device__ __forceinline__ float phi_h(const NodeCtx &n, int i, int a, float G) {
+  float e_C = n.dC[i][a] - (n.ux * n.gC[i][0] + n.uy * n.gC[i][1]);
+  float e_p = n.dp[a] - (n.ux * n.gp[0] + n.uy * n.gp[1]);
+  float e_Fs = n.mu[0] * n.dC[0][a] + n.mu[1] * n.dC[1][a] + n.mu[2] * n.dC[2][a] -
+               (n.ux * n.Fs[0] + n.uy * n.Fs[1]);
+  float e_Fb = (c_ex[a] - n.ux) * n.Fb[0] + (c_ey[a] - n.uy) * n.Fb[1];
+  return (e_C - n.C[i] / (n.rho * kCs2) * (e_p - e_Fs - e_Fb)) * G;
+}
+
+__device__ __forceinline__ bool node_of_thread(const DevParams &P, int &x, int &y) {
+  x = blockIdx.x * blockDim.x + threadIdx.x;
+  y = blockIdx.y * blockDim.y + threadIdx.y;
+  return x < P.nx && y < P.ny;
+}
+
+}  // namespace
+
+__global__ void k_moments(DevParams P, const float *__restrict__ h, float *__restrict__ C) {
+  int x, y;
+  if (!node_of_thread(P, x, y)) return;
+  const long long k = node_index(P, x, y);
+  for (int i = 0; i < P.nh; ++i) {
+    float s = 0.f;
+    for (int a = 0; a < 9; ++a) s += h[((long long)i * 9 + a) * P.plane + k];
+    C[(long long)i * P.plane + k] = s;
+  }
+}
+
+// rho, mu_1..3, u, p and (if write_tau) the new relaxation time and strain rate.
+__global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float *__restrict__ g,
+                         const float *__restrict__ tau_prev, float *__restrict__ mu, float *__restrict__ pf,
+                         float *__restrict__ uxf, float *__restrict__ uyf, float *__restrict__ tau_new,
+                         float *__restrict__ shear, unsigned *err, int write_tau) {
+  int x, y;
+  if (!node_of_thread(P, x, y)) return;
+  const long long k = node_index(P, x, y);
+  CReader cr{Cf, P.plane, P.nh};
+  float Cn[9][3], rn[9];
+  for (int a = 0; a < 9; ++a) {
+    long long kk = shifted(P, x, y, c_ex[a], c_ey[a]);
+    cr.at(kk, Cn[a]);
+    rn[a] = rho_of(P, Cn[a][0], Cn[a][1], Cn[a][2]);
+  }
+  NodeCtx n;
+  float lapC[3];
+  for (int j = 0; j < 3; ++j) {
+    n.C[j] = Cn[0][j];
+    float sx = 0.f, sy = 0.f, lp = 0.f;
+    for (int a = 0; a < 9; ++a) {
+      sx += c_w[a] * c_ex[a] * Cn[a][j];
+      sy += c_w[a] * c_ey[a] * Cn[a][j];
+      lp += c_w[a] * (Cn[a][j] - Cn[0][j]);
+    }
+    n.gC[j][0] = 3.0f * sx;
+    n.gC[j][1] = 3.0f * sy;
+    lapC[j] = 6.0f * lp;
+  }
+  n.rho = rn[0];
+  {
+    float sx = 0.f, sy = 0.f;
+    for (int a = 0; a < 9; ++a) {
+      sx += c_w[a] * c_ex[a] * rn[a];
+      sy += c_w[a] * c_ey[a] * rn[a];
+    }
+    n.grho[0] = 3.0f * sx;
+    n.grho[1] = 3.0f * sy;
+  }
+  chem_potentials(P, n.C, lapC, n.mu);
+  n.Fs[0] = n.mu[0] * n.gC[0][0] + n.mu[1] * n.gC[1][0] + n.mu[2] * n.gC[2][0];
+  n.Fs[1] = n.mu[0] * n.gC[0][1] + n.mu[1] * n.gC[1][1] + n.mu[2] * n.gC[2][1];
+  n.Fb[0] = P.force_x;
+  n.Fb[1] = -n.rho * P.gravity;
+  float ga[9], m0 = 0.f, mx = 0.f, my = 0.f;
+  for (int a = 0; a < 9; ++a) {
+    ga[a] = g[(long long)a * P.plane + k];
+    m0 += ga[a];
+    mx += c_ex[a] * ga[a];
+    my += c_ey[a] * ga[a];
+  }
+  n.ux = (3.0f * mx + 0.5f * (n.Fs[0] + n.Fb[0])) / n.rho;
+  n.uy = (3.0f * my + 0.5f * (n.Fs[1] + n.Fb[1])) / n.rho;
+  n.p = m0 + 0.5f * kCs2 * (n.ux * n.grho[0] + n.uy * n.grho[1]);
+  for (int j = 0; j < 3; ++j) mu[(long long)j * P.plane + k] = n.mu[j];
+  pf[k] = n.p;
+  uxf[k] = n.ux;
+  uyf[k] = n.uy;
+  if (!write_tau) return;
+  // directional derivatives of rho and C (the g forcing has no p derivative)
+  for (int a = 0; a < 9; ++a) {
+    const int o = c_opp[a];
+    float C2e[3] = {0.f, 0.f, 0.f}, r2e = 0.f;
+    if (P.fd_scheme == 1) {
+      cr.at(shifted(P, x, y, 2 * c_ex[a], 2 * c_ey[a]), C2e);
+      r2e = rho_of(P, C2e[0], C2e[1], C2e[2]);
+    }
+    for (int j = 0; j < 3; ++j) n.dC[j][a] = dir_deriv(P.fd_scheme, Cn[o][j], Cn[0][j], Cn[a][j], C2e[j]);
+    n.drho[a] = dir_deriv(P.fd_scheme, rn[o], rn[0], rn[a], r2e);
+  }
+  // strain rate from the non-equilibrium part with the previous tau (R23)
+  const float tp = tau_prev[k];
+  const float fac = 3.0f * (2.0f * tp / (2.0f * tp + 1.0f));
+  float Pxx = 0.f, Pyy = 0.f, Pxy = 0.f;
+  for (int a = 0; a < 9; ++a) {
+    float G = gamma_a(a, n.ux, n.uy);
+    float geq = c_w[a] * n.p + n.rho * kCs2 * (G - c_w[a]) - 0.5f * phi_g(n, a, G);
+    float fneq = fac * (ga[a] - geq);
+    Pxx += fneq * (float)(c_ex[a] * c_ex[a]);
+    Pyy += fneq * (float)(c_ey[a] * c_ey[a]);
+    Pxy += fneq * (float)(c_ex[a] * c_ey[a]);
+  }
+  const float den = 2.0f * tp * n.rho * kCs2;
+  const float Dxx = -Pxx / den, Dyy = -Pyy / den, Dxy = -Pxy / den;
+  const float gd = sqrtf(2.0f * (Dxx * Dxx + Dyy * Dyy + 2.0f * Dxy * Dxy));
+  const float tau1 = P.powerlaw ? tau_powerlaw(P, gd, n.rho) : P.tau[0];
+  const float tn = tau_mix(P, n.C[0], n.C[1], n.C[2], tau1);
+  tau_new[k] = tn;
+  shear[k] = gd;
+  if (!(isfinite(n.rho) && isfinite(n.p) && isfinite(n.ux) && isfinite(n.uy) && isfinite(tn))) atomicOr(err, 1u);
+}
+
+// S_i + V_i (Eq. 6, 18, 21; R8) for every transported order parameter.
+__global__ void k_sources(DevParams P, const float *__restrict__ Cf, const float *__restrict__ mu,
+                          float *__restrict__ SV) {
+  int x, y;
+  if (!node_of_thread(P, x, y)) return;
+  const long long k = node_index(P, x, y);
+  for (int i = 0; i < P.nh; ++i) {
+    const float *Ci = Cf + (long long)i * P.plane;
+    const float *mi = mu + (long long)i * P.plane;
+    float gcx = 0.f, gcy = 0.f, gmx = 0.f, gmy = 0.f, lm = 0.f;
+    const float m0 = mi[k];
+    for (int a = 0; a < 9; ++a) {
+      long long kk = shifted(P, x, y, c_ex[a], c_ey[a]);
+      float cv = Ci[kk], mv = mi[kk];
+      gcx += c_w[a] * c_ex[a] * cv;
+      gcy += c_w[a] * c_ey[a] * cv;
+      gmx += c_w[a] * c_ex[a] * mv;
+      gmy += c_w[a] * c_ey[a] * mv;
+      lm += c_w[a] * (mv - m0);
+    }
+    const float lapmu = 6.0f * lm;
+    const float C = Ci[k];
+    const float D0s = P.D0 / P.Sig[i];
+    float s;
+    if (P.mobility == 1) {
+      s = D0s * C * (1.0f - C) * lapmu + D0s * (1.0f - 2.0f * C) * (3.0f * gcx * 3.0f * gmx + 3.0f * gcy * 3.0f * gmy);
+    } else {
+      s = D0s * lapmu;
+    }
+    SV[(long long)i * P.plane + k] = s;
+  }
+}
+
+// Collision of g (Eq. 14) and h (Eq. 18, tau_h = 1/2) at each node, pushed to
+// x + e_a; populations that would cross a wall return to x in the opposite
+// direction.  With tau_h = 1/2 the BGK step of Eq. 18 replaces h by its
+// modified equilibrium, so h itself is not read: h* = C Gamma + Phi/2 + SV Gamma/2.
+__global__ void k_collide(DevParams P, const float *__restrict__ g, const float *__restrict__ Cf,
+                          const float *__restrict__ mu, const float *__restrict__ pf, const float *__restrict__ uxf,
+                          const float *__restrict__ uyf, const float *__restrict__ tau_new,
+                          const float *__restrict__ SV, float *__restrict__ g_out, float *__restrict__ h_out) {
+  int x, y;
+  if (!node_of_thread(P, x, y)) return;
+  const long long k = node_index(P, x, y);
+  CReader cr{Cf, P.plane, P.nh};
+  NodeCtx n;
+  gather_gradients(P, cr, pf, x, y, n);
+  n.ux = uxf[k];
+  n.uy = uyf[k];
+  for (int j = 0; j < 3; ++j) n.mu[j] = mu[(long long)j * P.plane + k];
+  n.Fs[0] = n.mu[0] * n.gC[0][0] + n.mu[1] * n.gC[1][0] + n.mu[2] * n.gC[2][0];
+  n.Fs[1] = n.mu[0] * n.gC[0][1] + n.mu[1] * n.gC[1][1] + n.mu[2] * n.gC[2][1];
+  n.Fb[0] = P.force_x;
+  n.Fb[1] = -n.rho * P.gravity;
+  const float omega = 1.0f / (tau_new[k] + 0.5f);
+  float sv[2] = {0.f, 0.f};
+  for (int i = 0; i < P.nh; ++i) sv[i] = SV[(long long)i * P.plane + k];
+  for (int a = 0; a < 9; ++a) {
+    const float G = gamma_a(a, n.ux, n.uy);
+    const float pg = phi_g(n, a, G);
+    const float geq = c_w[a] * n.p + n.rho * kCs2 * (G - c_w[a]) - 0.5f * pg;
+    const float gv = g[(long long)a * P.plane + k];
+    const float gstar = gv - omega * (gv - geq) + pg;
+    // destination
+    int dx = x + c_ex[a], dy = y + c_ey[a];
+    int da = a;
+    long long kd;
+    if (!P.periodic_y && (dy < 0 || dy >= P.ny)) {
+      kd = k;
+      da = c_opp[a];
+    } else {
+      kd = node_index(P, wrap_x(dx, P.nx), P.periodic_y ? wrap_y(dy, P.ny, 1) : dy);
+    }
+    g_out[(long long)da * P.plane + kd] = gstar;
+    const float Gd = gamma_a(da, uxf[kd], uyf[kd]);
+    for (int i = 0; i < P.nh; ++i) {
+      const float ph = phi_h(n, i, a, G);
+      const float hstar = n.C[i] * G + 0.5f * ph + 0.5f * sv[i] * G;
+      h_out[((long long)i * 9 + da) * P.plane + kd] = hstar + 0.5f * SV[(long long)i * P.plane + kd] * Gd;
+    }
+  }
+}
+
+// Modified equilibria (Eq. 16, 20) of given C, p, u, and tau at zero strain
+// rate (reading R11).  C, p, u are in the scratch planes.
+__global__ void k_init(DevParams P, const float *__restrict__ Cf, const float *__restrict__ pf,
+                       const float *__restrict__ uxf, const float *__restrict__ uyf, float *__restrict__ g,
+                       float *__restrict__ h, float *__restrict__ tau) {
+  int x, y;
+  if (!node_of_thread(P, x, y)) return;
+  const long long k = node_index(P, x, y);
+  CReader cr{Cf, P.plane, P.nh};
+  NodeCtx n;
+  gather_gradients(P, cr, pf, x, y, n);
+  float Cn[9][3], lapC[3];
+  for (int a = 0; a < 9; ++a) cr.at(shifted(P, x, y, c_ex[a], c_ey[a]), Cn[a]);
+  for (int j = 0; j < 3; ++j) {
+    float lp = 0.f;
+    for (int a = 0; a < 9; ++a) lp += c_w[a] * (Cn[a][j] - Cn[0][j]);
+    lapC[j] = 6.0f * lp;
+  }
+  chem_potentials(P, n.C, lapC, n.mu);
+  n.ux = uxf[k];
+  n.uy = uyf[k];
+  n.Fs[0] = n.mu[0] * n.gC[0][0] + n.mu[1] * n.gC[1][0] + n.mu[2] * n.gC[2][0];
+  n.Fs[1] = n.mu[0] * n.gC[0][1] + n.mu[1] * n.gC[1][1] + n.mu[2] * n.gC[2][1];
+  n.Fb[0] = P.force_x;
+  n.Fb[1] = -n.rho * P.gravity;
+  for (int a = 0; a < 9; ++a) {
+    const float G = gamma_a(a, n.ux, n.uy);
+    g[(long long)a * P.plane + k] = c_w[a] * n.p + n.rho * kCs2 * (G - c_w[a]) - 0.5f * phi_g(n, a, G);
+    for (int i = 0; i < P.nh; ++i)
+      h[((long long)i * 9 + a) * P.plane + k] = n.C[i] * G - 0.5f * phi_h(n, i, a, G);
+  }
+  const float tau1 = P.powerlaw ? tau_powerlaw(P, 0.0f, n.rho) : P.tau[0];
+  tau[k] = tau_mix(P, n.C[0], n.C[1], n.C[2], tau1);
+}
+
+// FP64 observable sums of Sec. 3.1 and Eq. 43-44 over the current fields:
+// acc[0..10] = M1..3, M1..3 above 0.5, A, sum C_g x, sum C_g y, sum C_g ux,
+// sum C_g uy; ext[0..3] = xmin, -xmax, ymin, -ymax of C_g > 0.5 (atomicMin).
+__global__ void k_observables(DevParams P, const float *__restrict__ Cf, const float *__restrict__ uxf,
+                              const float *__restrict__ uyf, int gas_comp, double *acc, int *ext) {
+  int x, y;
+  const bool inside = node_of_thread(P, x, y);
+  double v[11];
+  for (int q = 0; q < 11; ++q) v[q] = 0.0;
+  int e[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
+  if (inside) {
+    const long long k = node_index(P, x, y);
+    float C[3];
+    CReader{Cf, P.plane, P.nh}.at(k, C);
+    for (int i = 0; i < 3; ++i) {
+      v[i] = C[i];
+      v[3 + i] = C[i] > 0.5f ? (double)C[i] : 0.0;
+    }
+    const double cg = C[gas_comp - 1];
+    v[6] = cg;
+    v[7] = cg * x;
+    v[8] = cg * y;
+    v[9] = cg * uxf[k];
+    v[10] = cg * uyf[k];
+    if (C[gas_comp - 1] > 0.5f) {
+      e[0] = x;
+      e[1] = -x;
+      e[2] = y;
+      e[3] = -y;
+    }
+  }
+  // warp reduction, then one atomic per warp
+  for (int off = 16; off > 0; off >>= 1) {
+    for (int q = 0; q < 11; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
+    for (int q = 0; q < 4; ++q) e[q] = min(e[q], __shfl_down_sync(0xffffffffu, e[q], off));
+  }
+  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  if (lane == 0) {
+    for (int q = 0; q < 11; ++q) atomicAdd(&acc[q], v[q]);
+    for (int q = 0; q < 4; ++q)
+      if (e[q] != 0x7fffffff) atomicMin(&ext[q], e[q]);
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static dim3 node_grid(const DevParams &P, dim3 blk) {
+  return dim3((P.nx + blk.x - 1) / blk.x, (P.ny + blk.y - 1) / blk.y);
+}
+
+void launch_split_step(const DevParams &P, const StepBuffers &B, cudaStream_t s, cudaEvent_t *ev) {
+  const dim3 blk(32, 8);
+  const dim3 grd = node_grid(P, blk);
+  if (ev) cudaEventRecord(ev[0], s);
+  k_moments<<<grd, blk, 0, s>>>(P, B.h_in, B.C);
+  if (ev) cudaEventRecord(ev[1], s);
+  k_fields<<<grd, blk, 0, s>>>(P, B.C, B.g_in, B.tau_in, B.mu, B.p, B.ux, B.uy, B.tau_out, B.shear, B.err, 1);
+  if (ev) cudaEventRecord(ev[2], s);
+  k_sources<<<grd, blk, 0, s>>>(P, B.C, B.mu, B.SV);
+  if (ev) cudaEventRecord(ev[3], s);
+  k_collide<<<grd, blk, 0, s>>>(P, B.g_in, B.C, B.mu, B.p, B.ux, B.uy, B.tau_out, B.SV, B.g_out, B.h_out);
+  if (ev) cudaEventRecord(ev[4], s);
+}
+
+void launch_macros(const DevParams &P, const StepBuffers &B, cudaStream_t s) {
+  const dim3 blk(32, 8);
+  const dim3 grd = node_grid(P, blk);
+  k_moments<<<grd, blk, 0, s>>>(P, B.h_in, B.C);
+  k_fields<<<grd, blk, 0, s>>>(P, B.C, B.g_in, B.tau_in, B.mu, B.p, B.ux, B.uy, nullptr, nullptr, B.err, 0);
+}
+
+void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s) {
+  const dim3 blk(32, 8);
+  k_init<<<node_grid(P, blk), blk, 0, s>>>(P, B.C, B.p, B.ux, B.uy, B.g_out, B.h_out, B.tau_out);
+}
+
+void launch_observables(const DevParams &P, const StepBuffers &B, int gas_comp, double *acc, int *ext,
+                        cudaStream_t s) {
+  const dim3 blk(32, 8);
+  k_observables<<<node_grid(P, blk), blk, 0, s>>>(P, B.C, B.ux, B.uy, gas_comp, acc, ext);
+}
+
+}  // namespace lbm

@@ -1,0 +1,299 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h`` (same names).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``liblbm_gb300.so`` built from ``csrc/`` for sm_103a.  PyTorch supplies the
+device arena and the stream.  There is no fallback: if the library or a GPU
+is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB
+_lib = None
+
+STATUS = {0: "LBM_OK", -1: "LBM_E_INVAL", -2: "LBM_E_NOMEM", -3: "LBM_E_CUDA", -4: "LBM_E_DIVERGED",
+          -5: "LBM_E_TIMEOUT", -6: "LBM_E_STATE", -7: "LBM_E_IO"}
+FIELD_IDS = {"C1": 0, "C2": 1, "C3": 2, "rho": 3, "p": 4, "ux": 5, "uy": 6, "tau": 7, "mu1": 8,
+             "mu2": 9, "mu3": 10, "g": 11, "h": 12, "shear": 13, "SV": 16}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("ncomp", ctypes.c_int), ("periodic_y", ctypes.c_int),
+        ("rho", ctypes.c_double * 3), ("tau", ctypes.c_double * 3),
+        ("powerlaw", ctypes.c_int), ("pl_n", ctypes.c_double), ("pl_k", ctypes.c_double),
+        ("tau_min", ctypes.c_double), ("tau_max", ctypes.c_double),
+        ("sigma12", ctypes.c_double), ("sigma13", ctypes.c_double), ("sigma23", ctypes.c_double),
+        ("Lambda", ctypes.c_double), ("xi", ctypes.c_double), ("D0", ctypes.c_double),
+        ("mobility", ctypes.c_int), ("gravity", ctypes.c_double), ("force_x", ctypes.c_double),
+        ("fd_scheme", ctypes.c_int), ("storage", ctypes.c_int), ("gas_comp", ctypes.c_int),
+    ]
+
+
+class lbm_bubble(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("r", ctypes.c_double), ("comp", ctypes.c_int)]
+
+
+class lbm_obs(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_longlong), ("mass", ctypes.c_double * 3), ("mass_thr", ctypes.c_double * 3),
+        ("area", ctypes.c_double), ("centroid", ctypes.c_double * 2), ("velocity", ctypes.c_double * 2),
+        ("rise_velocity", ctypes.c_double), ("y_integrated", ctypes.c_double), ("d_eq", ctypes.c_double),
+        ("aspect_E", ctypes.c_double), ("drag_coefficient", ctypes.c_double), ("Re", ctypes.c_double),
+        ("Eo", ctypes.c_double), ("Mo", ctypes.c_double), ("raw", ctypes.c_double * 15),
+    ]
+
+
+DEFAULTS = dict(periodic_y=0, rho=(1.0, 1.0, 1.0), tau=(0.5, 0.5, 0.5), powerlaw=0, pl_n=1.0,
+                pl_k=1.0 / 6.0, tau_min=0.01, tau_max=3.0, sigma12=1e-3, sigma13=1e-3, sigma23=1e-3,
+                Lambda=0.0, xi=4.0, D0=4.0 / 300.0, mobility=0, gravity=0.0, force_x=0.0, fd_scheme=0,
+                storage=0, gas_comp=3)
+
+EXPORTED = ["lbm_version", "lbm_required_bytes", "lbm_create", "lbm_init_bubbles", "lbm_set_fields",
+            "lbm_step", "lbm_observables", "lbm_get_field", "lbm_save", "lbm_load", "lbm_destroy",
+            "lbm_last_error", "lbm_postprocess", "lbm_kernels_per_step", "lbm_kernel_name",
+            "lbm_profile_step"]
+
+
+def load_library(path: str | None = None):
+    """Loads the CUDA library (building it first if it is missing)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        _build.build()
+    lib = ctypes.CDLL(p)
+    P = ctypes.POINTER
+    vp, d = ctypes.c_void_p, P(ctypes.c_double)
+    lib.lbm_version.restype = ctypes.c_int
+    lib.lbm_required_bytes.restype = ctypes.c_size_t
+    lib.lbm_required_bytes.argtypes = [P(lbm_params)]
+    lib.lbm_create.argtypes = [P(lbm_params), vp, ctypes.c_size_t, vp, P(vp)]
+    lib.lbm_init_bubbles.argtypes = [vp, P(lbm_bubble), ctypes.c_int, ctypes.c_ulonglong, ctypes.c_double]
+    lib.lbm_set_fields.argtypes = [vp, d, d, d, d]
+    lib.lbm_step.argtypes = [vp, ctypes.c_longlong]
+    lib.lbm_observables.argtypes = [vp, P(lbm_obs)]
+    lib.lbm_get_field.argtypes = [vp, ctypes.c_int, d, ctypes.c_size_t]
+    lib.lbm_save.argtypes = [vp, ctypes.c_char_p]
+    lib.lbm_load.argtypes = [vp, ctypes.c_char_p]
+    lib.lbm_destroy.argtypes = [vp]
+    lib.lbm_destroy.restype = None
+    lib.lbm_last_error.argtypes = [vp]
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    lib.lbm_postprocess.argtypes = [P(lbm_params), d, P(lbm_obs)]
+    lib.lbm_kernels_per_step.argtypes = [vp]
+    lib.lbm_kernel_name.argtypes = [vp, ctypes.c_int]
+    lib.lbm_kernel_name.restype = ctypes.c_char_p
+    lib.lbm_profile_step.argtypes = [vp, ctypes.c_longlong, d, ctypes.c_int]
+    for name in EXPORTED:
+        getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def make_params(params: dict) -> lbm_params:
+    full = dict(DEFAULTS)
+    full.update(params)
+    pr = lbm_params()
+    for name, ctype in lbm_params._fields_:
+        v = full[name]
+        if name in ("rho", "tau"):
+            setattr(pr, name, (ctypes.c_double * 3)(*[float(x) for x in v]))
+        elif ctype is ctypes.c_int:
+            setattr(pr, name, int(v))
+        else:
+            setattr(pr, name, float(v))
+    return pr
+
+
+def obs_to_dict(o: lbm_obs) -> dict:
+    out = {}
+    for name, _ in lbm_obs._fields_:
+        v = getattr(o, name)
+        out[name] = list(v) if hasattr(v, "__len__") else v
+    return out
+
+
+def _check(h, rc, what):
+    if rc != 0:
+        msg = load_library().lbm_last_error(h).decode() if h else ""
+        raise LbmError(rc, f"{what}: {msg}")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# --- the C ABI, same names ------------------------------------------------
+
+def lbm_version() -> int:
+    return load_library().lbm_version()
+
+
+def lbm_required_bytes(params) -> int:
+    pr = params if isinstance(params, lbm_params) else make_params(params)
+    return int(load_library().lbm_required_bytes(ctypes.byref(pr)))
+
+
+def lbm_create(params, arena_ptr: int, arena_bytes: int, stream_ptr: int):
+    pr = params if isinstance(params, lbm_params) else make_params(params)
+    h = ctypes.c_void_p()
+    rc = load_library().lbm_create(ctypes.byref(pr), ctypes.c_void_p(arena_ptr), arena_bytes,
+                                   ctypes.c_void_p(stream_ptr), ctypes.byref(h))
+    _check(None, rc, "lbm_create")
+    return h
+
+
+def lbm_init_bubbles(h, bubbles, seed=0, noise=0.0):
+    arr = (lbm_bubble * max(1, len(bubbles)))()
+    for i, (cx, cy, r, c) in enumerate(bubbles):
+        arr[i] = lbm_bubble(float(cx), float(cy), float(r), int(c))
+    _check(h, load_library().lbm_init_bubbles(h, arr, len(bubbles), int(seed), float(noise)), "lbm_init_bubbles")
+
+
+def lbm_set_fields(h, C, p=None, ux=None, uy=None):
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    keep = [C]
+    ptrs = [_dptr(C)]
+    for f in (p, ux, uy):
+        if f is None:
+            ptrs.append(None)
+        else:
+            a = np.ascontiguousarray(f, dtype=np.float64)
+            keep.append(a)
+            ptrs.append(_dptr(a))
+    _check(h, load_library().lbm_set_fields(h, *ptrs), "lbm_set_fields")
+
+
+def lbm_step(h, nsteps: int = 1):
+    _check(h, load_library().lbm_step(h, int(nsteps)), "lbm_step")
+
+
+def lbm_observables(h) -> dict:
+    o = lbm_obs()
+    _check(h, load_library().lbm_observables(h, ctypes.byref(o)), "lbm_observables")
+    return obs_to_dict(o)
+
+
+def lbm_get_field(h, name: str, nx: int, ny: int, nh: int) -> np.ndarray:
+    fid = FIELD_IDS[name]
+    if name == "g":
+        shape = (9, ny, nx)
+    elif name == "h":
+        shape = (nh, 9, ny, nx)
+    elif name == "SV":
+        shape = (nh, ny, nx)
+    else:
+        shape = (ny, nx)
+    out = np.empty(shape, dtype=np.float64)
+    _check(h, load_library().lbm_get_field(h, fid, _dptr(out), out.size), "lbm_get_field")
+    return out
+
+
+def lbm_save(h, path: str):
+    _check(h, load_library().lbm_save(h, path.encode()), "lbm_save")
+
+
+def lbm_load(h, path: str):
+    _check(h, load_library().lbm_load(h, path.encode()), "lbm_load")
+
+
+def lbm_destroy(h):
+    if h:
+        load_library().lbm_destroy(h)
+
+
+def lbm_last_error(h) -> str:
+    return load_library().lbm_last_error(h).decode()
+
+
+def lbm_postprocess(params, raw) -> dict:
+    pr = params if isinstance(params, lbm_params) else make_params(params)
+    r = np.ascontiguousarray(raw, dtype=np.float64)
+    o = lbm_obs()
+    _check(None, load_library().lbm_postprocess(ctypes.byref(pr), _dptr(r), ctypes.byref(o)), "lbm_postprocess")
+    return obs_to_dict(o)
+
+
+def lbm_kernels_per_step(h) -> int:
+    return int(load_library().lbm_kernels_per_step(h))
+
+
+def lbm_kernel_name(h, i: int) -> str:
+    return load_library().lbm_kernel_name(h, int(i)).decode()
+
+
+def lbm_profile_step(h, nsteps: int) -> dict:
+    k = lbm_kernels_per_step(h)
+    out = np.zeros(max(k, 1), dtype=np.float64)
+    _check(h, load_library().lbm_profile_step(h, int(nsteps), _dptr(out), out.size), "lbm_profile_step")
+    return {lbm_kernel_name(h, i): float(out[i]) for i in range(k)}
+
+
+class Lattice:
+    """A handle plus its torch-allocated device arena and stream."""
+
+    def __init__(self, params: dict, device="cuda", stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU path exists)")
+        self.params = dict(DEFAULTS)
+        self.params.update(params)
+        self.nx, self.ny = int(self.params["nx"]), int(self.params["ny"])
+        self.nh = int(self.params["ncomp"]) - 1
+        self._pr = make_params(self.params)
+        self.nbytes = lbm_required_bytes(self._pr)
+        if self.nbytes == 0:
+            raise LbmError(-1, "invalid parameters")
+        self.arena = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.arena.device)
+        self.h = lbm_create(self._pr, self.arena.data_ptr(), self.nbytes, self.stream.cuda_stream)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lbm_destroy(h)
+            self.h = None
+
+    def init_bubbles(self, bubbles, seed=0, noise=0.0):
+        lbm_init_bubbles(self.h, bubbles, seed, noise)
+
+    def set_fields(self, C, p=None, ux=None, uy=None):
+        lbm_set_fields(self.h, C, p, ux, uy)
+
+    def step(self, nsteps=1):
+        lbm_step(self.h, nsteps)
+
+    def observables(self) -> dict:
+        return lbm_observables(self.h)
+
+    def field(self, name) -> np.ndarray:
+        return lbm_get_field(self.h, name, self.nx, self.ny, self.nh)
+
+    def kernel_times(self, reps=5) -> dict:
+        """Mean device ms of each kernel of the step (advances `reps` steps)."""
+        return lbm_profile_step(self.h, reps)
+
+    def launches_per_step(self) -> int:
+        return lbm_kernels_per_step(self.h)
+
+    def save(self, path):
+        lbm_save(self.h, path)
+
+    def load(self, path):
+        lbm_load(self.h, path)
