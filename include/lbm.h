@@ -65,6 +65,12 @@ typedef struct {
   int fd_scheme;       /* directional derivatives: 0 central, 1 mixed central/biased */
   int storage;         /* population storage: 0 FP32 (only FP32 is accepted) */
   int gas_comp;        /* component whose moments lbm_observables reports (2 or 3) */
+  int collapse_h;      /* 0: the state holds the populations h^i (Eq. 17-20);
+                          1: it holds C_i = sum_a h_a^i instead.  With tau_h = 1/2 the
+                          collision of Eq. 18 reads h only through C_i, so both forms give
+                          the same C, g, tau up to FP32 summation order; form 1 moves
+                          88 instead of 152 bytes per node-step (2 components).  Needs
+                          fd_scheme 0; LBM_FIELD_H is then unavailable. */
 } lbm_params;
 
 /* A disc of component `comp` (Eq. 42 profile). */

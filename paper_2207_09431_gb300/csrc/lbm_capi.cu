@@ -41,7 +41,7 @@ Layout layout_of(const lbm_params &p) {
     return o;
   };
   L.g = take(2 * 9);
-  L.h = take(2 * 9 * (size_t)nh);
+  L.h = take(p.collapse_h ? 2 * (size_t)nh : 2 * 9 * (size_t)nh);
   L.tau = take(2);
   L.C = take(nh);
   L.mu = take(3);
@@ -66,6 +66,8 @@ const char *validate(const lbm_params *p) {
   if (p->mobility != 0 && p->mobility != 1) return "mobility must be 0 or 1";
   if (p->gas_comp != 2 && p->gas_comp != 3) return "gas_comp must be 2 or 3";
   if (p->ncomp == 2 && p->gas_comp != 3) return "with two components the gas is component 3";
+  if (p->collapse_h != 0 && p->collapse_h != 1) return "collapse_h must be 0 or 1";
+  if (p->collapse_h && p->fd_scheme != 0) return "the collapsed state form needs fd_scheme 0";
   for (int i = 0; i < 3; ++i)
     if (!(p->rho[i] > 0) || !(p->tau[i] > 0)) return "densities and relaxation times must be positive";
   const double S1 = p->sigma12 + p->sigma13 - p->sigma23;
@@ -90,6 +92,7 @@ lbm::DevParams dev_params(const lbm_params &p) {
   d.powerlaw = p.powerlaw ? 1 : 0;
   d.mobility = p.mobility;
   d.fd_scheme = p.fd_scheme;
+  d.collapse_h = p.collapse_h;
   for (int i = 0; i < 3; ++i) {
     d.rho[i] = (float)p.rho[i];
     d.tau[i] = (float)p.tau[i];
@@ -156,15 +159,41 @@ struct lbm_handle {
     last_error = std::string(where) + ": " + cudaGetErrorString(e);
     return LBM_E_CUDA;
   }
-  lbm::StepBuffers buffers(int in) const {
-    lbm::StepBuffers B{};
+  bool fused() const { return lbm::fused_supported(dp); }
+  lbm::FusedBuffers fused_buffers(int in, bool diag) const {
+    lbm::FusedBuffers B{};
     B.g_in = g[in];
     B.h_in = h[in];
     B.tau_in = tau[in];
     B.g_out = g[1 - in];
     B.h_out = h[1 - in];
     B.tau_out = tau[1 - in];
-    B.C = C;
+    B.shear = diag ? shear : nullptr;
+    B.SV = diag ? SV : nullptr;
+    B.err = err;
+    return B;
+  }
+  // One time step from buffer `cur` into the other one.
+  void launch_step(bool diag, cudaEvent_t *ev) {
+    if (fused()) {
+      if (ev) cudaEventRecord(ev[0], stream);
+      lbm::launch_fused_step(dp, fused_buffers(cur, diag), stream);
+      if (ev) cudaEventRecord(ev[1], stream);
+    } else {
+      lbm::launch_split_step(dp, buffers(cur), stream, ev);
+    }
+    cur = 1 - cur;
+  }
+  int kernels_per_step() const { return fused() ? 1 : lbm::kSplitKernels; }
+  lbm::StepBuffers buffers(int in) const {
+    lbm::StepBuffers B{};
+    B.g_in = g[in];
+    B.h_in = prm.collapse_h ? nullptr : h[in];
+    B.tau_in = tau[in];
+    B.g_out = g[1 - in];
+    B.h_out = h[1 - in];
+    B.tau_out = tau[1 - in];
+    B.C = prm.collapse_h ? h[in] : C;
     B.mu = mu;
     B.p = p;
     B.ux = ux;
@@ -242,7 +271,7 @@ lbm_status lbm_create(const lbm_params *p, void *dev_arena, size_t arena_bytes, 
   const int nh = p->ncomp - 1;
   for (int b = 0; b < 2; ++b) {
     h->g[b] = (float *)(h->arena + L.g) + (size_t)b * 9 * pf;
-    h->h[b] = (float *)(h->arena + L.h) + (size_t)b * 9 * nh * pf;
+    h->h[b] = (float *)(h->arena + L.h) + (size_t)b * (p->collapse_h ? 1 : 9) * nh * pf;
     h->tau[b] = (float *)(h->arena + L.tau) + (size_t)b * pf;
   }
   h->C = (float *)(h->arena + L.C);
@@ -282,6 +311,12 @@ lbm_status lbm_set_fields(lbm_handle *h, const double *C, const double *p, const
   if (e != cudaSuccess) return h->cuda_fail(e, "lbm_set_fields upload");
   // equilibria into buffer 0
   lbm::StepBuffers B = h->buffers(1);  // *_out of buffer index 1 is buffer 0
+  if (h->prm.collapse_h) {
+    B.C = h->C;
+    B.h_out = nullptr;
+    e = cudaMemcpyAsync(h->h[0], h->C, (size_t)nh * h->L.plane_bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "lbm_set_fields copy");
+  }
   lbm::launch_init(h->dp, B, h->stream);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -337,10 +372,7 @@ lbm_status lbm_step(lbm_handle *h, long long nsteps) {
   if (nsteps < 0) return h->fail(LBM_E_INVAL, "nsteps < 0");
   cudaError_t e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "lbm_step memset");
-  for (long long t = 0; t < nsteps; ++t) {
-    lbm::launch_split_step(h->dp, h->buffers(h->cur), h->stream);
-    h->cur = 1 - h->cur;
-  }
+  for (long long t = 0; t < nsteps; ++t) h->launch_step(t == nsteps - 1, nullptr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return h->cuda_fail(e, "lbm_step launch");
   unsigned flag = 0;
@@ -457,20 +489,24 @@ lbm_status lbm_get_field(lbm_handle *h, int id, double *out, size_t n) {
   cudaError_t e = cudaSuccess;
   switch (id) {
     case LBM_FIELD_G: e = download_planes(h, h->g[h->cur], out, 9); break;
-    case LBM_FIELD_H: e = download_planes(h, h->h[h->cur], out, 9 * nh); break;
+    case LBM_FIELD_H:
+      if (h->prm.collapse_h) return h->fail(LBM_E_STATE, "the collapsed state form stores no h populations");
+      e = download_planes(h, h->h[h->cur], out, 9 * nh);
+      break;
     case LBM_FIELD_TAU: e = download_planes(h, h->tau[h->cur], out, 1); break;
     case LBM_FIELD_SHEAR: e = download_planes(h, h->shear, out, 1); break;
     case LBM_FIELD_SV: e = download_planes(h, h->SV, out, nh); break;
     default: {
       lbm_status st = compute_macros(h);
       if (st != LBM_OK) return st;
-      if (id == LBM_FIELD_C1) e = download_planes(h, h->C, out, 1);
+      const float *Cp = h->buffers(h->cur).C;
+      if (id == LBM_FIELD_C1) e = download_planes(h, Cp, out, 1);
       else if (id == LBM_FIELD_C2) {
-        if (nh == 2) e = download_planes(h, h->C + pf, out, 1);
+        if (nh == 2) e = download_planes(h, Cp + pf, out, 1);
         else std::memset(out, 0, N * sizeof(double));
       } else if (id == LBM_FIELD_C3 || id == LBM_FIELD_RHO) {
         std::vector<double> c(2 * N, 0.0);
-        e = download_planes(h, h->C, c.data(), nh);
+        e = download_planes(h, Cp, c.data(), nh);
         if (e == cudaSuccess)
           for (size_t k = 0; k < N; ++k) {
             // C3 = 1 - C1 - C2 (Eq. 1); rho by the clipped mixture law (R1)
@@ -499,13 +535,14 @@ lbm_status lbm_save(lbm_handle *h, const char *path) {
   if (!h->initialized) return h->fail(LBM_E_STATE, "save before initial fields");
   const int nh = h->prm.ncomp - 1;
   const size_t pf = h->L.plane_bytes / sizeof(float);
-  const int nplanes = 9 + 9 * nh + 1;
+  const int hp = (h->prm.collapse_h ? 1 : 9) * nh;
+  const int nplanes = 9 + hp + 1;
   std::vector<float> buf((size_t)nplanes * pf);
   cudaError_t e = cudaMemcpyAsync(buf.data(), h->g[h->cur], 9 * pf * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(buf.data() + 9 * pf, h->h[h->cur], 9 * nh * pf * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+    e = cudaMemcpyAsync(buf.data() + 9 * pf, h->h[h->cur], hp * pf * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(buf.data() + (size_t)(9 + 9 * nh) * pf, h->tau[h->cur], pf * sizeof(float),
+    e = cudaMemcpyAsync(buf.data() + (size_t)(9 + hp) * pf, h->tau[h->cur], pf * sizeof(float),
                         cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "lbm_save");
@@ -529,7 +566,8 @@ lbm_status lbm_load(lbm_handle *h, const char *path) {
   long long hdr[2];
   const int nh = h->prm.ncomp - 1;
   const size_t pf = h->L.plane_bytes / sizeof(float);
-  const size_t count = (size_t)(9 + 9 * nh + 1) * pf;
+  const int hp = (h->prm.collapse_h ? 1 : 9) * nh;
+  const size_t count = (size_t)(9 + hp + 1) * pf;
   bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
             std::fread(&prm, sizeof(prm), 1, f) == 1 && std::fread(hdr, sizeof(hdr), 1, f) == 1;
   if (ok && (std::memcmp(&prm, &h->prm, sizeof(prm)) != 0 || hdr[1] != (long long)count)) {
@@ -542,9 +580,9 @@ lbm_status lbm_load(lbm_handle *h, const char *path) {
   if (!ok) return h->fail(LBM_E_IO, "truncated or foreign checkpoint");
   cudaError_t e = cudaMemcpyAsync(h->g[0], buf.data(), 9 * pf * sizeof(float), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->h[0], buf.data() + 9 * pf, 9 * nh * pf * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+    e = cudaMemcpyAsync(h->h[0], buf.data() + 9 * pf, hp * pf * sizeof(float), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->tau[0], buf.data() + (size_t)(9 + 9 * nh) * pf, pf * sizeof(float),
+    e = cudaMemcpyAsync(h->tau[0], buf.data() + (size_t)(9 + hp) * pf, pf * sizeof(float),
                         cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "lbm_load");
@@ -555,26 +593,23 @@ lbm_status lbm_load(lbm_handle *h, const char *path) {
   return LBM_OK;
 }
 
-int lbm_kernels_per_step(const lbm_handle *h) { return h ? lbm::kSplitKernels : 0; }
+int lbm_kernels_per_step(const lbm_handle *h) { return h ? h->kernels_per_step() : 0; }
 
 const char *lbm_kernel_name(const lbm_handle *h, int i) {
   static const char *names[lbm::kSplitKernels] = {"k_moments", "k_fields", "k_sources", "k_collide"};
-  if (!h || i < 0 || i >= lbm::kSplitKernels) return "";
-  return names[i];
+  if (!h || i < 0 || i >= h->kernels_per_step()) return "";
+  return h->fused() ? "k_step_fused" : names[i];
 }
 
 lbm_status lbm_profile_step(lbm_handle *h, long long nsteps, double *ms_per_kernel, int nkernels) {
   if (!h || !ms_per_kernel || nsteps < 1) return LBM_E_INVAL;
   if (!h->initialized) return h->fail(LBM_E_STATE, "profile before initial fields");
-  const int K = lbm::kSplitKernels;
+  const int K = h->kernels_per_step();
   if (nkernels < K) return h->fail(LBM_E_INVAL, "ms_per_kernel too small");
   std::vector<cudaEvent_t> ev((size_t)(K + 1) * nsteps);
   for (auto &e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) return h->fail(LBM_E_CUDA, "cudaEventCreate");
-  for (long long t = 0; t < nsteps; ++t) {
-    lbm::launch_split_step(h->dp, h->buffers(h->cur), h->stream, ev.data() + t * (K + 1));
-    h->cur = 1 - h->cur;
-  }
+  for (long long t = 0; t < nsteps; ++t) h->launch_step(false, ev.data() + t * (K + 1));
   cudaError_t e = cudaStreamSynchronize(h->stream);
   for (int i = 0; i < K; ++i) ms_per_kernel[i] = 0.0;
   for (long long t = 0; t < nsteps && e == cudaSuccess; ++t)

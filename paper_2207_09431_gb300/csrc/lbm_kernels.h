@@ -20,6 +20,18 @@ struct StepBuffers {
 // ev[nkernels] after the last one.
 constexpr int kSplitKernels = 4;
 void launch_split_step(const DevParams &P, const StepBuffers &B, cudaStream_t s, cudaEvent_t *ev = nullptr);
+// Buffers of the fused single-kernel step.  shear and SV may be null (no
+// diagnostics written).
+struct FusedBuffers {
+  const float *g_in, *h_in, *tau_in;
+  float *g_out, *h_out, *tau_out;
+  float *shear, *SV;
+  unsigned *err;
+};
+
+bool fused_supported(const DevParams &P);
+void launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s);
+
 void launch_macros(const DevParams &P, const StepBuffers &B, cudaStream_t s);
 void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s);
 void launch_observables(const DevParams &P, const StepBuffers &B, int gas_comp, double *acc, int *ext,

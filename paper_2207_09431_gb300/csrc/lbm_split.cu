@@ -341,8 +341,9 @@ __global__ void k_init(DevParams P, const float *__restrict__ Cf, const float *_
   for (int a = 0; a < 9; ++a) {
     const float G = gamma_a(a, n.ux, n.uy);
     g[(long long)a * P.plane + k] = c_w[a] * n.p + n.rho * kCs2 * (G - c_w[a]) - 0.5f * phi_g(n, a, G);
-    for (int i = 0; i < P.nh; ++i)
-      h[((long long)i * 9 + a) * P.plane + k] = n.C[i] * G - 0.5f * phi_h(n, i, a, G);
+    if (h)
+      for (int i = 0; i < P.nh; ++i)
+        h[((long long)i * 9 + a) * P.plane + k] = n.C[i] * G - 0.5f * phi_h(n, i, a, G);
   }
   const float tau1 = P.powerlaw ? tau_powerlaw(P, 0.0f, n.rho) : P.tau[0];
   tau[k] = tau_mix(P, n.C[0], n.C[1], n.C[2], tau1);
@@ -415,7 +416,7 @@ void launch_split_step(const DevParams &P, const StepBuffers &B, cudaStream_t s,
 void launch_macros(const DevParams &P, const StepBuffers &B, cudaStream_t s) {
   const dim3 blk(32, 8);
   const dim3 grd = node_grid(P, blk);
-  k_moments<<<grd, blk, 0, s>>>(P, B.h_in, B.C);
+  if (B.h_in) k_moments<<<grd, blk, 0, s>>>(P, B.h_in, B.C);  // null: the state holds C
   k_fields<<<grd, blk, 0, s>>>(P, B.C, B.g_in, B.tau_in, B.mu, B.p, B.ux, B.uy, nullptr, nullptr, B.err, 0);
 }
 

@@ -137,31 +137,35 @@ def paper_case(n=0.6, eotvos=10.0, density_ratio=1000.0, mobility=1, k=None):
     return p, [(L / 2.0, 0.6 * L, R, 3)]
 
 
-def three_comp_case(nx=256, mobility=0, seed=0):
+def three_comp_case(nx=256, mobility=0, seed=0, max_draws=100000):
     """Three components, fully periodic: matrix 1 (power law n = 0.6), two droplets
-    of component 2 (R = 20, 12) and a bubble of component 3 (R = 6) at seeded
-    non-overlapping centres; no gravity."""
+    of component 2 (R = 20, 12 at nx = 256, scaled with nx) and a bubble of 3
+    (R = 6, scaled) at seeded non-overlapping centres; no gravity."""
     xi = 4.0
     p = dict(nx=nx, ny=nx, ncomp=3, periodic_y=1, rho=(1.0, 1.0, 0.01), tau=(0.5, 0.5, 0.25),
              powerlaw=1, pl_n=0.6, pl_k=1e-2, tau_min=0.01, tau_max=3.0, sigma12=1e-3,
              sigma13=1e-3, sigma23=1e-3, Lambda=0.0, xi=xi, D0=xi / 300.0, mobility=mobility,
              gravity=0.0, force_x=0.0, fd_scheme=0, gas_comp=3)
-    radii = [(20.0, 2), (12.0, 2), (6.0, 3)]
-    rng_counter = 0
+    scale = nx / 256.0
+    radii = [(max(20.0 * scale, 4.0), 2), (max(12.0 * scale, 4.0), 2), (max(6.0 * scale, 3.0), 3)]
+    gap = 2 * xi * max(scale, 0.25)
     centres = []
-    while len(centres) < len(radii):
-        z = splitmix64_at(seed, [rng_counter, rng_counter + 1])
-        rng_counter += 2
+    for draw in range(max_draws):
+        if len(centres) == len(radii):
+            break
+        z = splitmix64_at(seed, [2 * draw, 2 * draw + 1])
         cx, cy = (z >> np.uint64(11)).astype(np.float64) * (nx / 9007199254740992.0)
         R, c = radii[len(centres)]
         ok = True
         for (ox, oy, oR, _) in centres:
             dx = min(abs(cx - ox), nx - abs(cx - ox))
             dy = min(abs(cy - oy), nx - abs(cy - oy))
-            if math.hypot(dx, dy) < R + oR + 2 * xi:
+            if math.hypot(dx, dy) < R + oR + gap:
                 ok = False
         if ok:
             centres.append((float(cx), float(cy), R, c))
+    if len(centres) < len(radii):
+        raise ValueError("could not place the discs without overlap")
     return p, centres
 
 

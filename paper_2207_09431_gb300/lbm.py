@@ -39,6 +39,7 @@ class lbm_params(ctypes.Structure):
         ("Lambda", ctypes.c_double), ("xi", ctypes.c_double), ("D0", ctypes.c_double),
         ("mobility", ctypes.c_int), ("gravity", ctypes.c_double), ("force_x", ctypes.c_double),
         ("fd_scheme", ctypes.c_int), ("storage", ctypes.c_int), ("gas_comp", ctypes.c_int),
+        ("collapse_h", ctypes.c_int),
     ]
 
 
@@ -59,7 +60,7 @@ class lbm_obs(ctypes.Structure):
 DEFAULTS = dict(periodic_y=0, rho=(1.0, 1.0, 1.0), tau=(0.5, 0.5, 0.5), powerlaw=0, pl_n=1.0,
                 pl_k=1.0 / 6.0, tau_min=0.01, tau_max=3.0, sigma12=1e-3, sigma13=1e-3, sigma23=1e-3,
                 Lambda=0.0, xi=4.0, D0=4.0 / 300.0, mobility=0, gravity=0.0, force_x=0.0, fd_scheme=0,
-                storage=0, gas_comp=3)
+                storage=0, gas_comp=3, collapse_h=0)
 
 EXPORTED = ["lbm_version", "lbm_required_bytes", "lbm_create", "lbm_init_bubbles", "lbm_set_fields",
             "lbm_step", "lbm_observables", "lbm_get_field", "lbm_save", "lbm_load", "lbm_destroy",
