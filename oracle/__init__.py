@@ -27,22 +27,30 @@ from .observables import postprocess  # noqa: F401  (re-export)
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
-_LIB_PATH = os.path.join(_BUILD_DIR, "liblbm_oracle.so")
-_lib = None
+_LIB_PATHS = {"f64": os.path.join(_BUILD_DIR, "liblbm_oracle.so"),
+              "f32": os.path.join(_BUILD_DIR, "liblbm_oracle_f32.so")}
+_libs = {}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into a shared library (gcc, no machine-specific flags)."""
+def build(force: bool = False, precision: str = "f64") -> str:
+    """Compile the oracle into a shared library (gcc, no machine-specific flags).
+
+    precision "f64" is the oracle.  "f32" compiles the same source with FP32
+    internals; the GPU parity tests use it only to measure the FP32 rounding
+    floor of the scheme on a case."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
+    path = _LIB_PATHS[precision]
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
+        return path
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_BUILD_DIR)
     os.close(fd)
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    if precision == "f32":
+        cmd.insert(1, "-DORACLE_REAL=float")
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 class _Params(ctypes.Structure):
@@ -62,11 +70,10 @@ class _Params(ctypes.Structure):
     ]
 
 
-def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
-    lib = ctypes.CDLL(build())
+def _load(precision: str = "f64"):
+    if precision in _libs:
+        return _libs[precision]
+    lib = ctypes.CDLL(build(precision=precision))
     P = ctypes.POINTER
     d = P(ctypes.c_double)
     lib.orc_create.restype = ctypes.c_void_p
@@ -81,7 +88,7 @@ def _load():
     lib.orc_get_field.restype = ctypes.c_longlong
     lib.orc_get_field.argtypes = [ctypes.c_void_p, ctypes.c_int, d]
     lib.orc_observables.argtypes = [ctypes.c_void_p, ctypes.c_int, d]
-    _lib = lib
+    _libs[precision] = lib
     return lib
 
 
@@ -102,8 +109,8 @@ class Oracle:
     """One FP64 lattice; ``params`` is a dict with the keys of ``DEFAULTS`` plus
     nx, ny, ncomp."""
 
-    def __init__(self, params: dict):
-        lib = _load()
+    def __init__(self, params: dict, precision: str = "f64"):
+        lib = _load(precision)
         full = dict(DEFAULTS)
         full.update(params)
         self.params = full

@@ -57,6 +57,14 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Internal precision.  FP64 is the oracle; the same source compiled with
+ * -DORACLE_REAL=float measures the FP32 rounding floor of the scheme (test
+ * yardstick only).  Parameters and every API array stay double. */
+#ifndef ORACLE_REAL
+#define ORACLE_REAL double
+#endif
+typedef ORACLE_REAL real;
+
 typedef struct {
   int nx, ny, ncomp, periodic_y;
   double rho[3];   /* component densities */
@@ -75,28 +83,28 @@ typedef struct {
 /* D2Q9 (Eq. 10, 11): 0 rest, 1-4 = E N W S, 5-8 = NE NW SW SE. */
 static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-static const double W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+static const real W[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-static const double CS2 = 1.0 / 3.0;
+static const real CS2 = 1.0 / 3.0;
 
 typedef struct {
   orc_params p;
   int nh;          /* number of transported order parameters (ncomp - 1) */
   size_t n;        /* nodes */
   long long step;
-  double Sig[3], SigT;  /* capillary coefficients Sigma_i and Sigma_T (Sec. 2.1) */
+  real Sig[3], SigT;  /* capillary coefficients Sigma_i and Sigma_T (Sec. 2.1) */
   /* state */
-  double *g, *h, *tau;          /* g[9][n], h[nh][9][n], tau[n] (previous-step tau) */
-  double *gpost, *hpost;        /* post-collision buffers */
+  real *g, *h, *tau;          /* g[9][n], h[nh][9][n], tau[n] (previous-step tau) */
+  real *gpost, *hpost;        /* post-collision buffers */
   /* intermediate whole fields, recomputed every step */
-  double *C[3], *rho, *lapC[3], *mu[3], *gCx[3], *gCy[3], *grx, *gry;
-  double *Fsx, *Fsy, *Fbx, *Fby, *ux, *uy, *pr;
-  double *gpx, *gpy, *gmux[3], *gmuy[3], *lapmu[3];
-  double *tau_new, *shear, *S[2], *V[2];
+  real *C[3], *rho, *lapC[3], *mu[3], *gCx[3], *gCy[3], *grx, *gry;
+  real *Fsx, *Fsy, *Fbx, *Fby, *ux, *uy, *pr;
+  real *gpx, *gpy, *gmux[3], *gmuy[3], *lapmu[3];
+  real *tau_new, *shear, *S[2], *V[2];
   /* per-direction whole fields [9][n]: directional derivatives of rho, C_j, p;
    * forcing terms and modified equilibria of g and h */
-  double *drho, *dC[3], *dp, *Phig, *Phih[2], *geqb, *heqb[2];
+  real *drho, *dC[3], *dp, *Phig, *Phih[2], *geqb, *heqb[2];
   /* node index of x + e_a and x + 2 e_a under the ghost rule of reading R10 */
   size_t *nb1, *nb2;
 } orc_state;
@@ -122,16 +130,16 @@ static size_t wrap_index(const orc_state *s, int x, int y) {
 }
 
 /* Value of field f at node k shifted by d * e_a (d = 1 or 2). */
-static double at(const orc_state *s, const double *f, size_t k, int a, int d) {
+static real at(const orc_state *s, const real *f, size_t k, int a, int d) {
   return f[(d == 1 ? s->nb1 : s->nb2)[(size_t)a * s->n + k]];
 }
 
 /* Isotropic gradient (reading R2). */
-static void grad_iso(const orc_state *s, const double *f, double *gx, double *gy) {
+static void grad_iso(const orc_state *s, const real *f, real *gx, real *gy) {
   for (size_t k = 0; k < s->n; ++k) {
-    double sx = 0.0, sy = 0.0;
+    real sx = 0.0, sy = 0.0;
     for (int a = 0; a < 9; ++a) {
-      double v = at(s, f, k, a, 1);
+      real v = at(s, f, k, a, 1);
       sx += W[a] * EX[a] * v;
       sy += W[a] * EY[a] * v;
     }
@@ -141,40 +149,40 @@ static void grad_iso(const orc_state *s, const double *f, double *gx, double *gy
 }
 
 /* Isotropic Laplacian (reading R2). */
-static void lap_iso(const orc_state *s, const double *f, double *out) {
+static void lap_iso(const orc_state *s, const real *f, real *out) {
   for (size_t k = 0; k < s->n; ++k) {
-    double c = f[k], acc = 0.0;
+    real c = f[k], acc = 0.0;
     for (int a = 0; a < 9; ++a) acc += W[a] * (at(s, f, k, a, 1) - c);
     out[k] = 2.0 * acc / CS2;
   }
 }
 
 /* Directional derivative e_a . grad X at node (x, y) (reading R2). */
-static double dir_deriv(const orc_state *s, const double *f, size_t k, int a) {
-  double xp = at(s, f, k, a, 1);
-  double xm = at(s, f, k, OPP[a], 1);
+static real dir_deriv(const orc_state *s, const real *f, size_t k, int a) {
+  real xp = at(s, f, k, a, 1);
+  real xm = at(s, f, k, OPP[a], 1);
   if (s->p.fd_scheme == 0) return 0.5 * (xp - xm);
   /* mixed: average of the central and the second-order biased difference */
-  double xpp = at(s, f, k, a, 2);
-  double x0 = f[k];
-  double central = 0.5 * (xp - xm);
-  double biased = 0.5 * (-xpp + 4.0 * xp - 3.0 * x0);
+  real xpp = at(s, f, k, a, 2);
+  real x0 = f[k];
+  real central = 0.5 * (xp - xm);
+  real biased = 0.5 * (-xpp + 4.0 * xp - 3.0 * x0);
   return 0.5 * (central + biased);
 }
 
 /* Gamma_a(u) = f_a^eq / rho (Eq. 9). */
-static double Gamma(int a, double ux, double uy) {
-  double eu = EX[a] * ux + EY[a] * uy;
-  double uu = ux * ux + uy * uy;
+static real Gamma(int a, real ux, real uy) {
+  real eu = EX[a] * ux + EY[a] * uy;
+  real uu = ux * ux + uy * uy;
   return W[a] * (1.0 + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
 }
 
 /* Partial derivatives of the bulk free energy E0 (Eq. 3) with respect to
  * C1, C2, C3 taken as independent variables. */
-static void dE0(const orc_state *s, double C1, double C2, double C3, double d[3]) {
-  const double s12 = s->p.sigma12, s13 = s->p.sigma13, s23 = s->p.sigma23, L = s->p.Lambda;
-  const double S1 = s->Sig[0], S2 = s->Sig[1], S3 = s->Sig[2];
-  double mix = S1 * C1 + S2 * C2 + S3 * C3;
+static void dE0(const orc_state *s, real C1, real C2, real C3, real d[3]) {
+  const real s12 = s->p.sigma12, s13 = s->p.sigma13, s23 = s->p.sigma23, L = s->p.Lambda;
+  const real S1 = s->Sig[0], S2 = s->Sig[1], S3 = s->Sig[2];
+  real mix = S1 * C1 + S2 * C2 + S3 * C3;
   d[0] = 2.0 * s12 * C1 * C2 * C2 + 2.0 * s13 * C1 * C3 * C3 + C2 * C3 * mix + C1 * C2 * C3 * S1 +
          2.0 * L * C1 * C2 * C2 * C3 * C3;
   d[1] = 2.0 * s12 * C1 * C1 * C2 + 2.0 * s23 * C2 * C3 * C3 + C1 * C3 * mix + C1 * C2 * C3 * S2 +
@@ -185,17 +193,17 @@ static void dE0(const orc_state *s, double C1, double C2, double C3, double d[3]
 
 /* Power-law relaxation time of component 1 at strain rate gd and local
  * mixture density rho: Eq. 31 and Eq. 32, truncated as in Eq. 33 (reading R4). */
-static double tau_powerlaw(const orc_state *s, double gd, double rho) {
-  double eta = s->p.pl_k * pow(gd, s->p.pl_n - 1.0);
-  double t = eta / (rho * CS2);
+static real tau_powerlaw(const orc_state *s, real gd, real rho) {
+  real eta = s->p.pl_k * pow(gd, s->p.pl_n - 1.0);
+  real t = eta / (rho * CS2);
   if (!(t <= s->p.tau_max)) t = s->p.tau_max; /* also catches +inf at gd == 0, n < 1 */
   if (t < s->p.tau_min) t = s->p.tau_min;
   return t;
 }
 
 /* Mixture weights of reading R1. */
-static void mixture_weights(double C1, double C2, double C3, double c[3]) {
-  double v[3] = {C1, C2, C3}, sum = 0.0;
+static void mixture_weights(real C1, real C2, real C3, real c[3]) {
+  real v[3] = {C1, C2, C3}, sum = 0.0;
   for (int i = 0; i < 3; ++i) {
     c[i] = v[i] < 0.0 ? 0.0 : (v[i] > 1.0 ? 1.0 : v[i]);
     sum += c[i];
@@ -203,14 +211,14 @@ static void mixture_weights(double C1, double C2, double C3, double c[3]) {
   for (int i = 0; i < 3; ++i) c[i] /= sum;
 }
 
-static double rho_mixture(const orc_state *s, double C1, double C2, double C3) {
-  double c[3];
+static real rho_mixture(const orc_state *s, real C1, real C2, real C3) {
+  real c[3];
   mixture_weights(C1, C2, C3, c);
   return c[0] * s->p.rho[0] + c[1] * s->p.rho[1] + c[2] * s->p.rho[2];
 }
 
-static double tau_mixture(const orc_state *s, size_t k, double tau1) {
-  double c[3];
+static real tau_mixture(const orc_state *s, size_t k, real tau1) {
+  real c[3];
   mixture_weights(s->C[0][k], s->C[1][k], s->C[2][k], c);
   return c[0] * tau1 + c[1] * s->p.tau[1] + c[2] * s->p.tau[2];
 }
@@ -223,7 +231,7 @@ static double tau_mixture(const orc_state *s, size_t k, double tau1) {
 static void compute_macros(orc_state *s) {
   const size_t n = s->n;
   for (size_t k = 0; k < n; ++k) {
-    double c[2] = {0.0, 0.0};
+    real c[2] = {0.0, 0.0};
     for (int i = 0; i < s->nh; ++i)
       for (int a = 0; a < 9; ++a) c[i] += s->h[((size_t)i * 9 + a) * n + k];
     s->C[0][k] = c[0];
@@ -233,10 +241,10 @@ static void compute_macros(orc_state *s) {
   }
   for (int i = 0; i < 3; ++i) lap_iso(s, s->C[i], s->lapC[i]);
   for (size_t k = 0; k < n; ++k) {
-    double d[3];
+    real d[3];
     dE0(s, s->C[0][k], s->C[1][k], s->C[2][k], d);
     for (int i = 0; i < 3; ++i) {
-      double bulk = 0.0;
+      real bulk = 0.0;
       for (int j = 0; j < 3; ++j)
         if (j != i) bulk += (d[i] - d[j]) / s->Sig[j];
       s->mu[i][k] = 4.0 * s->SigT / s->p.xi * bulk - 0.75 * s->p.xi * s->Sig[i] * s->lapC[i][k];
@@ -245,7 +253,7 @@ static void compute_macros(orc_state *s) {
   for (int i = 0; i < 3; ++i) grad_iso(s, s->C[i], s->gCx[i], s->gCy[i]);
   grad_iso(s, s->rho, s->grx, s->gry);
   for (size_t k = 0; k < n; ++k) {
-    double fx = 0.0, fy = 0.0;
+    real fx = 0.0, fy = 0.0;
     for (int j = 0; j < 3; ++j) {
       fx += s->mu[j][k] * s->gCx[j][k];
       fy += s->mu[j][k] * s->gCy[j][k];
@@ -254,9 +262,9 @@ static void compute_macros(orc_state *s) {
     s->Fsy[k] = fy;
     s->Fbx[k] = s->p.force_x;
     s->Fby[k] = -s->rho[k] * s->p.gravity;
-    double mx = 0.0, my = 0.0, m0 = 0.0;
+    real mx = 0.0, my = 0.0, m0 = 0.0;
     for (int a = 0; a < 9; ++a) {
-      double ga = s->g[(size_t)a * n + k];
+      real ga = s->g[(size_t)a * n + k];
       m0 += ga;
       mx += EX[a] * ga;
       my += EY[a] * ga;
@@ -269,28 +277,28 @@ static void compute_macros(orc_state *s) {
 
 /* Forcing term of Eq. 14 for direction a at node (x, y):
  * (e_a - u).[grad(rho) cs^2 (Gamma_a - Gamma_a(0)) + (sum_j mu_j grad C_j + F_b) Gamma_a]. */
-static double forcing_g(const orc_state *s, size_t k, int a) {
+static real forcing_g(const orc_state *s, size_t k, int a) {
   const size_t n = s->n;
-  double ux = s->ux[k], uy = s->uy[k];
-  double G = Gamma(a, ux, uy);
-  double e_rho = s->drho[(size_t)a * n + k] - (ux * s->grx[k] + uy * s->gry[k]);
-  double e_Fs = -(ux * s->Fsx[k] + uy * s->Fsy[k]);
+  real ux = s->ux[k], uy = s->uy[k];
+  real G = Gamma(a, ux, uy);
+  real e_rho = s->drho[(size_t)a * n + k] - (ux * s->grx[k] + uy * s->gry[k]);
+  real e_Fs = -(ux * s->Fsx[k] + uy * s->Fsy[k]);
   for (int j = 0; j < 3; ++j) e_Fs += s->mu[j][k] * s->dC[j][(size_t)a * n + k];
-  double e_Fb = (EX[a] - ux) * s->Fbx[k] + (EY[a] - uy) * s->Fby[k];
+  real e_Fb = (EX[a] - ux) * s->Fbx[k] + (EY[a] - uy) * s->Fby[k];
   return e_rho * CS2 * (G - W[a]) + (e_Fs + e_Fb) * G;
 }
 
 /* Forcing term of Eq. 18 for order parameter i, direction a at (x, y):
  * (e_a - u).[grad C_i - C_i/(rho cs^2) (grad p - sum_j mu_j grad C_j - F_b)] Gamma_a. */
-static double forcing_h(const orc_state *s, int i, size_t k, int a) {
+static real forcing_h(const orc_state *s, int i, size_t k, int a) {
   const size_t n = s->n;
-  double ux = s->ux[k], uy = s->uy[k];
-  double G = Gamma(a, ux, uy);
-  double e_C = s->dC[i][(size_t)a * n + k] - (ux * s->gCx[i][k] + uy * s->gCy[i][k]);
-  double e_p = s->dp[(size_t)a * n + k] - (ux * s->gpx[k] + uy * s->gpy[k]);
-  double e_Fs = -(ux * s->Fsx[k] + uy * s->Fsy[k]);
+  real ux = s->ux[k], uy = s->uy[k];
+  real G = Gamma(a, ux, uy);
+  real e_C = s->dC[i][(size_t)a * n + k] - (ux * s->gCx[i][k] + uy * s->gCy[i][k]);
+  real e_p = s->dp[(size_t)a * n + k] - (ux * s->gpx[k] + uy * s->gpy[k]);
+  real e_Fs = -(ux * s->Fsx[k] + uy * s->Fsy[k]);
   for (int j = 0; j < 3; ++j) e_Fs += s->mu[j][k] * s->dC[j][(size_t)a * n + k];
-  double e_Fb = (EX[a] - ux) * s->Fbx[k] + (EY[a] - uy) * s->Fby[k];
+  real e_Fb = (EX[a] - ux) * s->Fbx[k] + (EY[a] - uy) * s->Fby[k];
   return (e_C - s->C[i][k] / (s->rho[k] * CS2) * (e_p - e_Fs - e_Fb)) * G;
 }
 
@@ -314,10 +322,10 @@ static void forcing_and_equilibria(orc_state *s) {
   for (int a = 0; a < 9; ++a)
     for (size_t k = 0; k < n; ++k) {
       size_t ak = (size_t)a * n + k;
-      double G = Gamma(a, s->ux[k], s->uy[k]);
+      real G = Gamma(a, s->ux[k], s->uy[k]);
       s->Phig[ak] = forcing_g(s, k, a);
-      double feq = s->rho[k] * G;
-      double geq = feq * CS2 + (s->pr[k] - s->rho[k] * CS2) * W[a];
+      real feq = s->rho[k] * G;
+      real geq = feq * CS2 + (s->pr[k] - s->rho[k] * CS2) * W[a];
       s->geqb[ak] = geq - 0.5 * s->Phig[ak];
       for (int i = 0; i < s->nh; ++i) {
         s->Phih[i][ak] = forcing_h(s, i, k, a);
@@ -347,29 +355,29 @@ orc_state *orc_create(const orc_params *prm) {
   }
   s->SigT = 3.0 / (1.0 / s->Sig[0] + 1.0 / s->Sig[1] + 1.0 / s->Sig[2]);
   size_t n = s->n;
-  s->g = calloc(9 * n, sizeof(double));
-  s->gpost = calloc(9 * n, sizeof(double));
-  s->h = calloc((size_t)s->nh * 9 * n, sizeof(double));
-  s->hpost = calloc((size_t)s->nh * 9 * n, sizeof(double));
-  s->tau = calloc(n, sizeof(double));
-  double **fields[] = {&s->rho, &s->grx, &s->gry, &s->Fsx, &s->Fsy, &s->Fbx, &s->Fby, &s->ux,
+  s->g = calloc(9 * n, sizeof(real));
+  s->gpost = calloc(9 * n, sizeof(real));
+  s->h = calloc((size_t)s->nh * 9 * n, sizeof(real));
+  s->hpost = calloc((size_t)s->nh * 9 * n, sizeof(real));
+  s->tau = calloc(n, sizeof(real));
+  real **fields[] = {&s->rho, &s->grx, &s->gry, &s->Fsx, &s->Fsy, &s->Fbx, &s->Fby, &s->ux,
                        &s->uy, &s->pr, &s->gpx, &s->gpy, &s->tau_new, &s->shear};
-  for (size_t f = 0; f < sizeof(fields) / sizeof(fields[0]); ++f) *fields[f] = calloc(n, sizeof(double));
+  for (size_t f = 0; f < sizeof(fields) / sizeof(fields[0]); ++f) *fields[f] = calloc(n, sizeof(real));
   for (int i = 0; i < 3; ++i) {
-    s->C[i] = calloc(n, sizeof(double));
-    s->lapC[i] = calloc(n, sizeof(double));
-    s->mu[i] = calloc(n, sizeof(double));
-    s->gCx[i] = calloc(n, sizeof(double));
-    s->gCy[i] = calloc(n, sizeof(double));
-    s->gmux[i] = calloc(n, sizeof(double));
-    s->gmuy[i] = calloc(n, sizeof(double));
-    s->lapmu[i] = calloc(n, sizeof(double));
+    s->C[i] = calloc(n, sizeof(real));
+    s->lapC[i] = calloc(n, sizeof(real));
+    s->mu[i] = calloc(n, sizeof(real));
+    s->gCx[i] = calloc(n, sizeof(real));
+    s->gCy[i] = calloc(n, sizeof(real));
+    s->gmux[i] = calloc(n, sizeof(real));
+    s->gmuy[i] = calloc(n, sizeof(real));
+    s->lapmu[i] = calloc(n, sizeof(real));
   }
   for (int i = 0; i < 2; ++i) {
-    s->S[i] = calloc(n, sizeof(double));
-    s->V[i] = calloc(n, sizeof(double));
-    s->Phih[i] = calloc(9 * n, sizeof(double));
-    s->heqb[i] = calloc(9 * n, sizeof(double));
+    s->S[i] = calloc(n, sizeof(real));
+    s->V[i] = calloc(n, sizeof(real));
+    s->Phih[i] = calloc(9 * n, sizeof(real));
+    s->heqb[i] = calloc(9 * n, sizeof(real));
   }
   s->nb1 = calloc(9 * n, sizeof(size_t));
   s->nb2 = calloc(9 * n, sizeof(size_t));
@@ -379,18 +387,18 @@ orc_state *orc_create(const orc_params *prm) {
         s->nb1[(size_t)a * n + idx(s, x, y)] = wrap_index(s, x + EX[a], y + EY[a]);
         s->nb2[(size_t)a * n + idx(s, x, y)] = wrap_index(s, x + 2 * EX[a], y + 2 * EY[a]);
       }
-  s->drho = calloc(9 * n, sizeof(double));
-  s->dp = calloc(9 * n, sizeof(double));
-  for (int j = 0; j < 3; ++j) s->dC[j] = calloc(9 * n, sizeof(double));
-  s->Phig = calloc(9 * n, sizeof(double));
-  s->geqb = calloc(9 * n, sizeof(double));
+  s->drho = calloc(9 * n, sizeof(real));
+  s->dp = calloc(9 * n, sizeof(real));
+  for (int j = 0; j < 3; ++j) s->dC[j] = calloc(9 * n, sizeof(real));
+  s->Phig = calloc(9 * n, sizeof(real));
+  s->geqb = calloc(9 * n, sizeof(real));
   return s;
 }
 
 void orc_destroy(orc_state *s) {
   if (!s) return;
   free(s->g); free(s->gpost); free(s->h); free(s->hpost); free(s->tau);
-  double *fields[] = {s->rho, s->grx, s->gry, s->Fsx, s->Fsy, s->Fbx, s->Fby, s->ux,
+  real *fields[] = {s->rho, s->grx, s->gry, s->Fsx, s->Fsy, s->Fbx, s->Fby, s->ux,
                       s->uy,  s->pr,  s->gpx, s->gpy, s->tau_new, s->shear};
   for (size_t f = 0; f < sizeof(fields) / sizeof(fields[0]); ++f) free(fields[f]);
   for (int i = 0; i < 3; ++i) {
@@ -419,10 +427,10 @@ int orc_set_fields(orc_state *s, const double *C, const double *p, const double 
   }
   for (int i = 0; i < 3; ++i) lap_iso(s, s->C[i], s->lapC[i]);
   for (size_t k = 0; k < n; ++k) {
-    double d[3];
+    real d[3];
     dE0(s, s->C[0][k], s->C[1][k], s->C[2][k], d);
     for (int i = 0; i < 3; ++i) {
-      double bulk = 0.0;
+      real bulk = 0.0;
       for (int j = 0; j < 3; ++j)
         if (j != i) bulk += (d[i] - d[j]) / s->Sig[j];
       s->mu[i][k] = 4.0 * s->SigT / s->p.xi * bulk - 0.75 * s->p.xi * s->Sig[i] * s->lapC[i][k];
@@ -432,7 +440,7 @@ int orc_set_fields(orc_state *s, const double *C, const double *p, const double 
   grad_iso(s, s->rho, s->grx, s->gry);
   grad_iso(s, s->pr, s->gpx, s->gpy);
   for (size_t k = 0; k < n; ++k) {
-    double fx = 0.0, fy = 0.0;
+    real fx = 0.0, fy = 0.0;
     for (int j = 0; j < 3; ++j) {
       fx += s->mu[j][k] * s->gCx[j][k];
       fy += s->mu[j][k] * s->gCy[j][k];
@@ -449,7 +457,7 @@ int orc_set_fields(orc_state *s, const double *C, const double *p, const double 
       s->g[(size_t)a * n + k] = s->geqb[(size_t)a * n + k];
       for (int i = 0; i < s->nh; ++i) s->h[((size_t)i * 9 + a) * n + k] = s->heqb[i][(size_t)a * n + k];
     }
-    double tau1 = s->p.powerlaw ? tau_powerlaw(s, 0.0, s->rho[k]) : s->p.tau[0];
+    real tau1 = s->p.powerlaw ? tau_powerlaw(s, 0.0, s->rho[k]) : s->p.tau[0];
     s->tau[k] = tau_mixture(s, k, tau1);
   }
   s->step = 0;
@@ -532,28 +540,28 @@ static void one_step(orc_state *s) {
    * rho cs^2 belongs to the barred populations, so with the un-barred f^neq of
    * Eq. 29 it is 2 tau rho cs^2 (the two forms give the same D). */
   for (size_t k = 0; k < n; ++k) {
-    double tp = s->tau[k];
-    double Pxx = 0.0, Pyy = 0.0, Pxy = 0.0;
+    real tp = s->tau[k];
+    real Pxx = 0.0, Pyy = 0.0, Pxy = 0.0;
     for (int a = 0; a < 9; ++a) {
-      double fneq = (1.0 / CS2) * (2.0 * tp / (2.0 * tp + 1.0)) *
+      real fneq = (1.0 / CS2) * (2.0 * tp / (2.0 * tp + 1.0)) *
                     (s->g[(size_t)a * n + k] - s->geqb[(size_t)a * n + k]);
       Pxx += fneq * EX[a] * EX[a];
       Pyy += fneq * EY[a] * EY[a];
       Pxy += fneq * EX[a] * EY[a];
     }
-    double den = 2.0 * tp * s->rho[k] * CS2;
-    double Dxx = -Pxx / den, Dyy = -Pyy / den, Dxy = -Pxy / den;
-    double gd = sqrt(2.0 * (Dxx * Dxx + Dyy * Dyy + 2.0 * Dxy * Dxy));
+    real den = 2.0 * tp * s->rho[k] * CS2;
+    real Dxx = -Pxx / den, Dyy = -Pyy / den, Dxy = -Pxy / den;
+    real gd = sqrt(2.0 * (Dxx * Dxx + Dyy * Dyy + 2.0 * Dxy * Dxy));
     s->shear[k] = gd;
-    double tau1 = s->p.powerlaw ? tau_powerlaw(s, gd, s->rho[k]) : s->p.tau[0];
+    real tau1 = s->p.powerlaw ? tau_powerlaw(s, gd, s->rho[k]) : s->p.tau[0];
     s->tau_new[k] = tau_mixture(s, k, tau1);
   }
   /* Diffusion sources of Eq. 18: S_i = D_i lap(mu_i) (Eq. 6) and, for the
    * variable mobility, V_i of Eq. 21 (reading R8). */
   for (int i = 0; i < s->nh; ++i)
     for (size_t k = 0; k < n; ++k) {
-      double Ci = s->C[i][k];
-      double D = s->p.D0 / s->Sig[i];
+      real Ci = s->C[i][k];
+      real D = s->p.D0 / s->Sig[i];
       if (s->p.mobility == 1) D *= Ci * (1.0 - Ci);
       s->S[i][k] = D * s->lapmu[i][k];
       s->V[i][k] = (s->p.mobility == 1)
@@ -562,16 +570,16 @@ static void one_step(orc_state *s) {
                        : 0.0;
     }
   /* Collision (Eq. 14 and Eq. 18 with tau_h = 0.5, source-side terms). */
-  const double tau_h = 0.5;
+  const real tau_h = 0.5;
   for (int a = 0; a < 9; ++a)
     for (size_t k = 0; k < n; ++k) {
       size_t ak = (size_t)a * n + k;
-      double ga = s->g[ak];
+      real ga = s->g[ak];
       s->gpost[ak] = ga - (ga - s->geqb[ak]) / (s->tau_new[k] + 0.5) + s->Phig[ak];
-      double G = Gamma(a, s->ux[k], s->uy[k]);
+      real G = Gamma(a, s->ux[k], s->uy[k]);
       for (int i = 0; i < s->nh; ++i) {
         size_t iak = (size_t)i * 9 * n + ak;
-        double ha = s->h[iak];
+        real ha = s->h[iak];
         s->hpost[iak] = ha - (ha - s->heqb[i][ak]) / (tau_h + 0.5) + s->Phih[i][ak] +
                         0.5 * (s->S[i][k] + s->V[i][k]) * G;
       }
@@ -599,13 +607,13 @@ static void one_step(orc_state *s) {
           aa = a;
         }
         s->g[(size_t)a * n + k] = s->gpost[(size_t)aa * n + src];
-        double G = Gamma(a, s->ux[k], s->uy[k]);
+        real G = Gamma(a, s->ux[k], s->uy[k]);
         for (int i = 0; i < s->nh; ++i)
           s->h[((size_t)i * 9 + a) * n + k] =
               s->hpost[((size_t)i * 9 + aa) * n + src] + 0.5 * (s->S[i][k] + s->V[i][k]) * G;
       }
     }
-  memcpy(s->tau, s->tau_new, n * sizeof(double));
+  memcpy(s->tau, s->tau_new, n * sizeof(real));
   s->step += 1;
 }
 
@@ -615,6 +623,10 @@ int orc_step(orc_state *s, long long nsteps) {
 }
 
 long long orc_get_step(const orc_state *s) { return s->step; }
+
+static void copy_out(double *out, const real *src, size_t n) {
+  for (size_t k = 0; k < n; ++k) out[k] = (double)src[k];
+}
 
 /* Field ids (macroscopic fields are those of the current populations). */
 enum {
@@ -627,20 +639,20 @@ enum {
 long long orc_get_field(orc_state *s, int id, double *out) {
   const size_t n = s->n;
   switch (id) {
-    case ORC_G: memcpy(out, s->g, 9 * n * sizeof(double)); return (long long)(9 * n);
-    case ORC_H: memcpy(out, s->h, (size_t)s->nh * 9 * n * sizeof(double)); return (long long)(s->nh * 9 * n);
-    case ORC_TAU: memcpy(out, s->tau, n * sizeof(double)); return (long long)n;
-    case ORC_SHEAR: memcpy(out, s->shear, n * sizeof(double)); return (long long)n;
+    case ORC_G: copy_out(out, s->g, 9 * n); return (long long)(9 * n);
+    case ORC_H: copy_out(out, s->h, (size_t)s->nh * 9 * n); return (long long)(s->nh * 9 * n);
+    case ORC_TAU: copy_out(out, s->tau, n); return (long long)n;
+    case ORC_SHEAR: copy_out(out, s->shear, n); return (long long)n;
     case ORC_S:
-      for (int i = 0; i < s->nh; ++i) memcpy(out + (size_t)i * n, s->S[i], n * sizeof(double));
+      for (int i = 0; i < s->nh; ++i) copy_out(out + (size_t)i * n, s->S[i], n);
       return (long long)(s->nh * n);
     case ORC_V:
-      for (int i = 0; i < s->nh; ++i) memcpy(out + (size_t)i * n, s->V[i], n * sizeof(double));
+      for (int i = 0; i < s->nh; ++i) copy_out(out + (size_t)i * n, s->V[i], n);
       return (long long)(s->nh * n);
     default: break;
   }
   compute_macros(s);
-  const double *src = NULL;
+  const real *src = NULL;
   switch (id) {
     case ORC_C1: src = s->C[0]; break;
     case ORC_C2: src = s->C[1]; break;
@@ -654,7 +666,7 @@ long long orc_get_field(orc_state *s, int id, double *out) {
     case ORC_MU3: src = s->mu[2]; break;
     default: return -1;
   }
-  memcpy(out, src, n * sizeof(double));
+  copy_out(out, src, n);
   return (long long)n;
 }
 
@@ -668,7 +680,7 @@ void orc_observables(orc_state *s, int gas_comp, double *out) {
   compute_macros(s);
   for (int i = 0; i < 15; ++i) out[i] = 0.0;
   double xmin = -1, xmax = -1, ymin = -1, ymax = -1;
-  const double *Cg = s->C[gas_comp - 1];
+  const real *Cg = s->C[gas_comp - 1];
   for (int y = 0; y < s->p.ny; ++y)
     for (int x = 0; x < s->p.nx; ++x) {
       size_t k = idx(s, x, y);
