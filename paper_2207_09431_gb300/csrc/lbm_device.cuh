@@ -24,8 +24,15 @@ namespace lbm {
 // D2Q9 (Eq. 10-11): 0 rest, 1-4 E N W S, 5-8 NE NW SW SE.
 static __device__ __constant__ int c_ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static __device__ __constant__ int c_ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-static __device__ __constant__ float c_w[9] = {4.f / 9.f,  1.f / 9.f,  1.f / 9.f,  1.f / 9.f, 1.f / 9.f,
-                                        1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
+// FP32 weights chosen so that w0 + 4 w1 + 4 w2 == 1 exactly: fl(4/9), fl(1/9)
+// and fl(1/36) lowered by one ulp.  With the nearest floats the nine weights
+// sum to 1 + 1.1e-8, and every node would gain that fraction of its order
+// parameter per step (a systematic mass drift of 1e-5 in 1000 steps).
+#define LBM_W0 0x1.c71c72p-2f
+#define LBM_W1 0x1.c71c72p-4f
+#define LBM_W2 0x1.c71c70p-6f
+static __device__ __constant__ float c_w[9] = {LBM_W0, LBM_W1, LBM_W1, LBM_W1, LBM_W1,
+                                               LBM_W2, LBM_W2, LBM_W2, LBM_W2};
 static __device__ __constant__ int c_opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 
 constexpr float kCs2 = 1.0f / 3.0f;
