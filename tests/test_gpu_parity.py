@@ -117,11 +117,15 @@ def test_small_rising_bubble_1000_steps(lbm):
     c = Case(lbm, p, C)
     c.step(1000)
     c.check()
-    og, oo = c.lat.observables(), c.orc.observables()
+    og, oo, o32 = c.lat.observables(), c.orc.observables(), c.o32.observables()
     assert abs(og["rise_velocity"] - oo["rise_velocity"]) <= 5e-3 * abs(oo["rise_velocity"])
-    assert abs(og["centroid"][1] - oo["centroid"][1]) < 1e-3
+    # centroid and masses: FP32 rounding of C accumulates into the sums; the
+    # FP32 build of the oracle sets the scale
+    dy32 = abs(o32["centroid"][1] - oo["centroid"][1])
+    assert abs(og["centroid"][1] - oo["centroid"][1]) <= max(1e-3, FLOOR_FACTOR * dy32)
     for i in (0, 2):
-        assert abs(og["mass"][i] - oo["mass"][i]) < 1e-5 * oo["mass"][i]
+        floor = abs(o32["mass"][i] - oo["mass"][i]) / oo["mass"][i]
+        assert abs(og["mass"][i] - oo["mass"][i]) / oo["mass"][i] <= max(1e-6, FLOOR_FACTOR * floor)
 
 
 def test_three_components_periodic(lbm):
@@ -149,12 +153,11 @@ def test_observables_match_oracle(lbm):
     c.step(50)
     raw = np.array(c.lat.observables()["raw"])
     ref, r32 = c.orc.raw_observables(), c.o32.raw_observables()
-    # masses and centroid sums: FP64 sums of FP32 fields
-    assert np.allclose(raw[:9], ref[:9], rtol=1e-6, atol=1e-9)
-    # velocity moments follow the velocity field's floor
-    for q in (9, 10):
+    # masses, centroid and velocity sums: FP64 sums of FP32 fields, within the
+    # deviation of the FP32 build of the oracle
+    for q in (0, 2, 3, 5, 6, 7, 8, 9, 10):
         floor = abs(r32[q] - ref[q]) / abs(ref[q])
-        assert abs(raw[q] - ref[q]) / abs(ref[q]) <= max(TOL, FLOOR_FACTOR * floor)
+        assert abs(raw[q] - ref[q]) / abs(ref[q]) <= max(1e-6, FLOOR_FACTOR * floor), q
     # extents of C_g > 0.5: integers; a node within FP32 rounding of 0.5 may flip by one
     assert np.max(np.abs(raw[11:] - ref[11:])) <= 1
 
