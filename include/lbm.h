@@ -42,7 +42,8 @@ typedef enum {
   LBM_E_DIVERGED = -4, /* a non-finite rho, p, u or tau appeared during lbm_step */
   LBM_E_TIMEOUT = -5,  /* a bounded device wait ran out */
   LBM_E_STATE = -6,    /* call out of order (e.g. lbm_step before initial fields) */
-  LBM_E_IO = -7        /* checkpoint file could not be read or written */
+  LBM_E_IO = -7,       /* checkpoint file could not be read or written */
+  LBM_E_RANGE = -8     /* input larger than a fixed maximum (see LBM_STATIC_MAX_NODES) */
 } lbm_status;
 
 /* Problem statement of Sec. 2 (Eq. 1-33) plus the set-up of Sec. 3-4. */
@@ -176,6 +177,34 @@ const char *lbm_last_error(const lbm_handle *h);
  * sum C_g ux, sum C_g uy, xmin, xmax, ymin, ymax}.  step and y_integrated are
  * left at 0. */
 lbm_status lbm_postprocess(const lbm_params *p, const double raw[15], lbm_obs *out);
+
+/* Largest lattice (nx * ny nodes) lbm_observables_static accepts. */
+#define LBM_STATIC_MAX_NODES (1 << 20)
+
+/* Observables of a state held in the caller's own device buffers, for callers
+ * that cannot allocate device memory: a program that manages the whole device
+ * budget itself and only hands out fixed buffers cannot provide the arena that
+ * lbm_create needs just to ask for the masses or the rise velocity of a state
+ * it already holds.  This call allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine): its reduction scratch is a fixed array of about
+ * 416 KiB that every GPU loading the library keeps until the process exits.
+ * The paper has no counterpart; the sums are those of lbm_observables.
+ *
+ * p: lattice parameters (nx * ny <= LBM_STATIC_MAX_NODES, else LBM_E_RANGE).
+ * g: device pointer to the 9 planes of the populations g (Eq. 14-16).
+ * hc: device pointer to the (ncomp - 1) x 9 planes of h (collapse_h == 0) or
+ *     the (ncomp - 1) planes of C (collapse_h == 1).
+ * pitch: floats per row (>= nx); plane_stride: floats per plane (>= pitch * ny);
+ *     node (x, y) of plane q is at q * plane_stride + y * pitch + x.
+ * raw_out: host array of 15 doubles, the layout of lbm_postprocess.
+ * cuda_stream: stream the two kernels run on; the call waits for it.
+ * The first call on a device looks up the device address of the scratch
+ * array; make it before any stream capture on that device.  Calls that
+ * overlap on the GPU (other streams, other host threads) race on the shared
+ * scratch array.  Returns LBM_E_INVAL for bad arguments, LBM_E_CUDA if a CUDA
+ * call fails. */
+lbm_status lbm_observables_static(const lbm_params *p, const float *g, const float *hc, int pitch,
+                                  long long plane_stride, double raw_out[15], void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,8 @@ LIB_PATH = _build.LIB
 _lib = None
 
 STATUS = {0: "LBM_OK", -1: "LBM_E_INVAL", -2: "LBM_E_NOMEM", -3: "LBM_E_CUDA", -4: "LBM_E_DIVERGED",
-          -5: "LBM_E_TIMEOUT", -6: "LBM_E_STATE", -7: "LBM_E_IO"}
+          -5: "LBM_E_TIMEOUT", -6: "LBM_E_STATE", -7: "LBM_E_IO", -8: "LBM_E_RANGE"}
+STATIC_MAX_NODES = 1 << 20
 FIELD_IDS = {"C1": 0, "C2": 1, "C3": 2, "rho": 3, "p": 4, "ux": 5, "uy": 6, "tau": 7, "mu1": 8,
              "mu2": 9, "mu3": 10, "g": 11, "h": 12, "shear": 13, "SV": 16}
 
@@ -65,7 +66,7 @@ DEFAULTS = dict(periodic_y=0, rho=(1.0, 1.0, 1.0), tau=(0.5, 0.5, 0.5), powerlaw
 EXPORTED = ["lbm_version", "lbm_required_bytes", "lbm_create", "lbm_init_bubbles", "lbm_set_fields",
             "lbm_step", "lbm_observables", "lbm_get_field", "lbm_save", "lbm_load", "lbm_destroy",
             "lbm_last_error", "lbm_postprocess", "lbm_kernels_per_step", "lbm_kernel_name",
-            "lbm_profile_step"]
+            "lbm_profile_step", "lbm_observables_static"]
 
 
 def load_library(path: str | None = None):
@@ -99,6 +100,7 @@ def load_library(path: str | None = None):
     lib.lbm_kernel_name.argtypes = [vp, ctypes.c_int]
     lib.lbm_kernel_name.restype = ctypes.c_char_p
     lib.lbm_profile_step.argtypes = [vp, ctypes.c_longlong, d, ctypes.c_int]
+    lib.lbm_observables_static.argtypes = [P(lbm_params), vp, vp, ctypes.c_int, ctypes.c_longlong, d, vp]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     if path is None:
@@ -243,6 +245,19 @@ def lbm_profile_step(h, nsteps: int) -> dict:
     out = np.zeros(max(k, 1), dtype=np.float64)
     _check(h, load_library().lbm_profile_step(h, int(nsteps), _dptr(out), out.size), "lbm_profile_step")
     return {lbm_kernel_name(h, i): float(out[i]) for i in range(k)}
+
+
+def lbm_observables_static(params, g_ptr: int, hc_ptr: int, pitch: int, plane_stride: int,
+                           stream_ptr: int = 0) -> np.ndarray:
+    """Raw observable sums (15 doubles) of a state in caller-held device buffers;
+    allocates no device memory (see include/lbm.h)."""
+    pr = params if isinstance(params, lbm_params) else make_params(params)
+    out = np.zeros(15, dtype=np.float64)
+    rc = load_library().lbm_observables_static(ctypes.byref(pr), ctypes.c_void_p(g_ptr), ctypes.c_void_p(hc_ptr),
+                                               int(pitch), int(plane_stride), _dptr(out),
+                                               ctypes.c_void_p(stream_ptr))
+    _check(None, rc, "lbm_observables_static")
+    return out
 
 
 class Lattice:
