@@ -162,6 +162,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     lat = lbm.Lattice(p, device=dev, stream=stream)
     lat.set_fields(C)
+    kernel_config = lat.autotune(reps=5)
     lat.step(args.warmup)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -229,6 +230,7 @@ def run_ours(args):
         "roofline": roofline, "e2e": e2e, "clocks": clk,
         "gpu_launches": lat.launches_per_step() * args.steps,
         "kernel_ms": {k: round(v, 5) for k, v in kt.items()},
+        "kernel_config": kernel_config,
         "observables_after": {"rise_velocity": obs["rise_velocity"], "mass1": obs["mass"][0]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -163,6 +163,19 @@ void lbm_destroy(lbm_handle *h);
 int lbm_kernels_per_step(const lbm_handle *h);
 const char *lbm_kernel_name(const lbm_handle *h, int i);
 
+/* Times each launch configuration of the fused step (tile shape, threads per
+ * CTA, CTAs per SM) for `reps` launches from the current state into the spare
+ * buffer, without advancing the state, and keeps the fastest for lbm_step.
+ * chosen (may be NULL) receives its index; lbm_kernel_name reports its name.
+ * Synchronises the stream.  Handles start with configuration 0. */
+lbm_status lbm_autotune(lbm_handle *h, int reps, int *chosen);
+
+/* Number of launch configurations of the step, and explicit selection of one
+ * (for example a saved lbm_autotune result).  Every configuration computes the
+ * same values. */
+int lbm_kernel_config_count(const lbm_handle *h);
+lbm_status lbm_set_kernel_config(lbm_handle *h, int config);
+
 /* Measurement: advances nsteps time steps (they count as steps of the run)
  * recording a CUDA event on the handle's stream around every kernel, and
  * returns the mean device time of each kernel in ms_per_kernel[0..k-1],

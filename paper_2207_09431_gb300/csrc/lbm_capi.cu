@@ -115,6 +115,15 @@ lbm::DevParams dev_params(const lbm_params &p) {
   d.SigT = (float)(3.0 / (1.0 / S1 + 1.0 / S2 + 1.0 / S3));
   d.xi = (float)p.xi;
   d.D0 = (float)p.D0;
+  const double Sg[3] = {S1, S2, S3};
+  for (int i = 0; i < 3; ++i) {
+    d.inv_sig[i] = (float)(1.0 / Sg[i]);
+    d.grad_coef[i] = (float)(0.75 * p.xi * Sg[i]);
+    d.d0_sig[i] = (float)(p.D0 / Sg[i]);
+  }
+  d.mu_pre = (float)(4.0 * (3.0 / (1.0 / S1 + 1.0 / S2 + 1.0 / S3)) / p.xi);
+  d.n1 = (float)(p.pl_n - 1.0);
+  d.k3 = (float)(3.0 * p.pl_k);
   d.gravity = (float)p.gravity;
   d.force_x = (float)p.force_x;
   d.plane = (long long)p.ny * d.pitch;
@@ -143,6 +152,8 @@ struct lbm_handle {
   int *ext;
   unsigned *err;
   int cur;
+  int variant;            // fused-step launch configuration (autotuned or 0)
+  std::string kname;      // name reported by lbm_kernel_name
   bool initialized;
   long long step;
   bool have_prev;
@@ -177,7 +188,7 @@ struct lbm_handle {
   void launch_step(bool diag, cudaEvent_t *ev) {
     if (fused()) {
       if (ev) cudaEventRecord(ev[0], stream);
-      lbm::launch_fused_step(dp, fused_buffers(cur, diag), stream);
+      lbm::launch_fused_step(dp, fused_buffers(cur, diag), stream, variant);
       if (ev) cudaEventRecord(ev[1], stream);
     } else {
       lbm::launch_split_step(dp, buffers(cur), stream, ev);
@@ -287,6 +298,7 @@ lbm_status lbm_create(const lbm_params *p, void *dev_arena, size_t arena_bytes, 
   // plane stride used by the kernels must match the arena planes
   h->dp.plane = (long long)pf;
   h->cur = 0;
+  h->variant = 0;
   h->initialized = false;
   h->step = 0;
   h->have_prev = false;
@@ -598,7 +610,61 @@ int lbm_kernels_per_step(const lbm_handle *h) { return h ? h->kernels_per_step()
 const char *lbm_kernel_name(const lbm_handle *h, int i) {
   static const char *names[lbm::kSplitKernels] = {"k_moments", "k_fields", "k_sources", "k_collide"};
   if (!h || i < 0 || i >= h->kernels_per_step()) return "";
-  return h->fused() ? "k_step_fused" : names[i];
+  if (!h->fused()) return names[i];
+  lbm_handle *m = const_cast<lbm_handle *>(h);
+  m->kname = std::string("k_step_fused[") + lbm::fused_variant_name(h->dp, h->variant) + "]";
+  return m->kname.c_str();
+}
+
+int lbm_kernel_config_count(const lbm_handle *h) {
+  if (!h) return 0;
+  return h->fused() ? lbm::fused_variant_count(h->dp) : 1;
+}
+
+lbm_status lbm_set_kernel_config(lbm_handle *h, int config) {
+  if (!h) return LBM_E_INVAL;
+  if (config < 0 || config >= lbm_kernel_config_count(h)) return h->fail(LBM_E_INVAL, "no such kernel configuration");
+  h->variant = h->fused() ? config : 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_handle *h, int reps, int *chosen) {
+  if (!h || reps < 1) return LBM_E_INVAL;
+  if (!h->initialized) return h->fail(LBM_E_STATE, "autotune before initial fields");
+  if (!h->fused()) {
+    if (chosen) *chosen = 0;
+    return LBM_OK;
+  }
+  const int nv = lbm::fused_variant_count(h->dp);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return h->fail(LBM_E_CUDA, "cudaEventCreate");
+  // every candidate runs from the current state into the spare buffer; the
+  // state itself is not advanced
+  const lbm::FusedBuffers B = h->fused_buffers(h->cur, false);
+  int best = 0;
+  float best_ms = 0.f;
+  cudaError_t err = cudaSuccess;
+  for (int v = 0; v < nv && err == cudaSuccess; ++v) {
+    err = lbm::launch_fused_step(h->dp, B, h->stream, v);  // warm-up and attribute set-up
+    if (err != cudaSuccess) break;
+    cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < reps; ++r) lbm::launch_fused_step(h->dp, B, h->stream, v);
+    cudaEventRecord(e1, h->stream);
+    err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && (v == 0 || ms < best_ms)) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return h->cuda_fail(err, "lbm_autotune");
+  h->variant = best;
+  if (chosen) *chosen = best;
+  return LBM_OK;
 }
 
 lbm_status lbm_profile_step(lbm_handle *h, long long nsteps, double *ms_per_kernel, int nkernels) {

@@ -21,9 +21,9 @@
 
 namespace lbm {
 
-// D2Q9 (Eq. 10-11): 0 rest, 1-4 E N W S, 5-8 NE NW SW SE.
-static __device__ __constant__ int c_ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-static __device__ __constant__ int c_ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+// D2Q9 (Eq. 10-11): 0 rest, 1-4 E N W S, 5-8 NE NW SW SE.  Compile-time
+// functions, so that unrolled loops see immediates.
+//
 // FP32 weights chosen so that w0 + 4 w1 + 4 w2 == 1 exactly: fl(4/9), fl(1/9)
 // and fl(1/36) lowered by one ulp.  With the nearest floats the nine weights
 // sum to 1 + 1.1e-8, and every node would gain that fraction of its order
@@ -31,9 +31,11 @@ static __device__ __constant__ int c_ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 #define LBM_W0 0x1.c71c72p-2f
 #define LBM_W1 0x1.c71c72p-4f
 #define LBM_W2 0x1.c71c70p-6f
-static __device__ __constant__ float c_w[9] = {LBM_W0, LBM_W1, LBM_W1, LBM_W1, LBM_W1,
-                                               LBM_W2, LBM_W2, LBM_W2, LBM_W2};
-static __device__ __constant__ int c_opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+__host__ __device__ constexpr int ex(int a) { return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0); }
+__host__ __device__ constexpr int ey(int a) { return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0); }
+__host__ __device__ constexpr float wt(int a) { return a == 0 ? LBM_W0 : (a < 5 ? LBM_W1 : LBM_W2); }
+__host__ __device__ constexpr int opp(int a) { return a == 0 ? 0 : (a < 5 ? (a + 1) % 4 + 1 : (a - 3) % 4 + 5); }
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "D2Q9");
 
 constexpr float kCs2 = 1.0f / 3.0f;
 
@@ -49,9 +51,9 @@ __device__ __forceinline__ int wrap_y(int y, int ny, int periodic) {
 
 // Gamma_a(u) = f_a^eq / rho (Eq. 9).
 __device__ __forceinline__ float gamma_a(int a, float ux, float uy) {
-  float eu = c_ex[a] * ux + c_ey[a] * uy;
+  float eu = ex(a) * ux + ey(a) * uy;
   float uu = ux * ux + uy * uy;
-  return c_w[a] * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
+  return wt(a) * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
 }
 
 // Mixture weights of reading R1.
@@ -85,17 +87,22 @@ __device__ __forceinline__ void chem_potentials(const DevParams &P, const float 
              2.f * L * C1 * C1 * C2 * C3 * C3;
   float d2 = 2.f * P.sig13 * C1 * C1 * C3 + 2.f * P.sig23 * C2 * C2 * C3 + C1 * C2 * (mix + S3 * C3) +
              2.f * L * C1 * C1 * C2 * C2 * C3;
-  const float pre = 4.f * P.SigT / P.xi;
-  mu[0] = pre * ((d0 - d1) / S2 + (d0 - d2) / S3) - 0.75f * P.xi * S1 * lapC[0];
-  mu[1] = pre * ((d1 - d0) / S1 + (d1 - d2) / S3) - 0.75f * P.xi * S2 * lapC[1];
-  mu[2] = pre * ((d2 - d0) / S1 + (d2 - d1) / S2) - 0.75f * P.xi * S3 * lapC[2];
+  // (4 Sigma_T / xi) sum_{j != i} (d_i - d_j) / Sigma_j - (3/4) xi Sigma_i lap C_i
+  mu[0] = P.mu_pre * ((d0 - d1) * P.inv_sig[1] + (d0 - d2) * P.inv_sig[2]) - P.grad_coef[0] * lapC[0];
+  mu[1] = P.mu_pre * ((d1 - d0) * P.inv_sig[0] + (d1 - d2) * P.inv_sig[2]) - P.grad_coef[1] * lapC[1];
+  mu[2] = P.mu_pre * ((d2 - d0) * P.inv_sig[0] + (d2 - d1) * P.inv_sig[1]) - P.grad_coef[2] * lapC[2];
 }
 
-// Power-law relaxation time at strain rate gd (Eq. 31-33, reading R4).
-__device__ __forceinline__ float tau_powerlaw(const DevParams &P, float gd, float rho) {
-  float eta = P.pl_k * powf(gd, P.pl_n - 1.0f);
-  float t = eta / (rho * kCs2);
-  t = (t <= P.tau_max) ? t : P.tau_max;  // also maps +inf (gd == 0, n < 1) to tau_max
+// Power-law relaxation time at strain rate gd (Eq. 31-33, reading R4):
+// tau = k gd^(n-1) / (rho cs^2), clamped; irho = 1 / rho.
+__device__ __forceinline__ float tau_powerlaw(const DevParams &P, float gd, float irho) {
+  float t;
+  if (gd > 0.0f) {
+    t = P.k3 * exp2f(P.n1 * __log2f(gd)) * irho;
+  } else {  // zero strain rate: infinite (n < 1), zero (n > 1) or k (n = 1) viscosity
+    t = P.n1 < 0.0f ? __int_as_float(0x7f800000) : (P.n1 > 0.0f ? 0.0f : P.k3 * irho);
+  }
+  t = (t <= P.tau_max) ? t : P.tau_max;  // also maps +inf to tau_max
   return fmaxf(t, P.tau_min);
 }
 

@@ -11,6 +11,12 @@ struct DevParams {
   float pl_n, pl_k, tau_min, tau_max;
   float sig12, sig13, sig23, Lambda, Sig[3], SigT, xi, D0;
   float gravity, force_x;
+  // precomputed on the host (double, then rounded)
+  float inv_sig[3];    // 1 / Sigma_i
+  float mu_pre;        // 4 Sigma_T / xi (Eq. 5)
+  float grad_coef[3];  // (3/4) xi Sigma_i (Eq. 5)
+  float d0_sig[3];     // D0 / Sigma_i (Eq. 6)
+  float n1, k3;        // n - 1 and k / cs^2 (Eq. 31-32)
   long long plane;  // floats per plane (ny * pitch)
 };
 

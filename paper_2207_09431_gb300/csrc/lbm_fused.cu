@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffe
       const float ga = B.g_in[(long long)a * plane + k];
       s.g[a][q] = ga;
       m0 += ga;
-      mx += c_ex[a] * ga;
-      my += c_ey[a] * ga;
+      mx += ex(a) * ga;
+      my += ey(a) * ga;
     }
     float C[3], lap[3], gx[3], gyv[3], mu[3];
     float rx = 0.f, ry = 0.f;
@@ -136,22 +136,22 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffe
       float cc[3][9];
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        const int j3 = c0 + c_ey[a] * S::W3 + c_ex[a];
+        const int j3 = c0 + ey(a) * S::W3 + ex(a);
         cc[0][a] = s.C[0][j3];
         cc[1][a] = NH == 2 ? s.C[NH - 1][j3] : 0.f;
         cc[2][a] = 1.0f - cc[0][a] - cc[1][a];
         const float r = s.rho[j3];
-        rx += c_w[a] * c_ex[a] * r;
-        ry += c_w[a] * c_ey[a] * r;
+        rx += wt(a) * ex(a) * r;
+        ry += wt(a) * ey(a) * r;
       }
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         float sx = 0.f, sy = 0.f, lp = 0.f;
 #pragma unroll
         for (int a = 1; a < 9; ++a) {
-          sx += c_w[a] * c_ex[a] * cc[j][a];
-          sy += c_w[a] * c_ey[a] * cc[j][a];
-          lp += c_w[a] * (cc[j][a] - cc[j][0]);
+          sx += wt(a) * ex(a) * cc[j][a];
+          sy += wt(a) * ey(a) * cc[j][a];
+          lp += wt(a) * (cc[j][a] - cc[j][0]);
         }
         C[j] = cc[j][0];
         gx[j] = 3.0f * sx;
@@ -165,8 +165,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffe
     const float Fsx = mu[0] * gx[0] + mu[1] * gx[1] + mu[2] * gx[2];
     const float Fsy = mu[0] * gyv[0] + mu[1] * gyv[1] + mu[2] * gyv[2];
     const float rho = s.rho[i3<TX>(lx, ly)];
-    const float ux = (3.0f * mx + 0.5f * (Fsx + P.force_x)) / rho;
-    const float uy = (3.0f * my + 0.5f * (Fsy - rho * P.gravity)) / rho;
+    const float irho = 1.0f / rho;
+    const float ux = (3.0f * mx + 0.5f * (Fsx + P.force_x)) * irho;
+    const float uy = (3.0f * my + 0.5f * (Fsy - rho * P.gravity)) * irho;
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
       s.mu[i][q] = mu[i];
@@ -206,22 +207,23 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffe
     const int c2 = i2<TX>(lx, ly);
     const int c3 = i3<TX>(lx, ly);
     const float ux = s.ux[c2], uy = s.uy[c2], p = s.p[c2], rho = s.rho[c3];
+    const float irho = 1.0f / rho;
     // gradients of p and mu on R2
     float px = 0.f, py = 0.f, mgx[NH], mgy[NH], mlap[NH];
 #pragma unroll
     for (int i = 0; i < NH; ++i) mgx[i] = mgy[i] = mlap[i] = 0.f;
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
-      const int j2 = c2 + c_ey[a] * S::W2 + c_ex[a];
+      const int j2 = c2 + ey(a) * S::W2 + ex(a);
       const float pv = s.p[j2];
-      px += c_w[a] * c_ex[a] * pv;
-      py += c_w[a] * c_ey[a] * pv;
+      px += wt(a) * ex(a) * pv;
+      py += wt(a) * ey(a) * pv;
 #pragma unroll
       for (int i = 0; i < NH; ++i) {
         const float m = s.mu[i][j2];
-        mgx[i] += c_w[a] * c_ex[a] * m;
-        mgy[i] += c_w[a] * c_ey[a] * m;
-        mlap[i] += c_w[a] * (m - s.mu[i][c2]);
+        mgx[i] += wt(a) * ex(a) * m;
+        mgy[i] += wt(a) * ey(a) * m;
+        mlap[i] += wt(a) * (m - s.mu[i][c2]);
       }
     }
     px *= 3.0f;
@@ -234,14 +236,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffe
       Fsx += dmu[i] * gcx;
       Fsy += dmu[i] * gcy;
       Cc[i] = s.C[i][c3];
-      const float D0s = P.D0 / P.Sig[i];
+      const float D0s = P.d0_sig[i];
       const float lapmu = 6.0f * mlap[i];
       if (P.mobility == 1)
         sv[i] = D0s * Cc[i] * (1.0f - Cc[i]) * lapmu +
                 D0s * (1.0f - 2.0f * Cc[i]) * 3.0f * (gcx * mgx[i] + gcy * mgy[i]);
       else
         sv[i] = D0s * lapmu;
-      kap[i] = Cc[i] / (rho * kCs2);
+      kap[i] = 3.0f * Cc[i] * irho;  // C_i / (rho cs^2)
       udC[i] = ux * gcx + uy * gcy;
       s.sv[i][q] = sv[i];
     }
@@ -257,11 +259,11 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffe
     float Pxx = 0.f, Pyy = 0.f, Pxy = 0.f;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const float ex = (float)c_ex[a], ey = (float)c_ey[a], w = c_w[a];
-      const float eu = ex * ux + ey * uy;
+      const float exa = (float)ex(a), eya = (float)ey(a), w = wt(a);
+      const float eu = exa * ux + eya * uy;
       const float G = w * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-      const int jp3 = c3 + c_ey[a] * S::W3 + c_ex[a], jm3 = c3 - c_ey[a] * S::W3 - c_ex[a];
-      const int jp2 = c2 + c_ey[a] * S::W2 + c_ex[a], jm2 = c2 - c_ey[a] * S::W2 - c_ex[a];
+      const int jp3 = c3 + ey(a) * S::W3 + ex(a), jm3 = c3 - ey(a) * S::W3 - ex(a);
+      const int jp2 = c2 + ey(a) * S::W2 + ex(a), jm2 = c2 - ey(a) * S::W2 - ex(a);
       const float dr = 0.5f * (s.rho[jp3] - s.rho[jm3]);
       const float dp = 0.5f * (s.p[jp2] - s.p[jm2]);
       float dC[NH];
@@ -271,15 +273,15 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffe
         dC[i] = 0.5f * (s.C[i][jp3] - s.C[i][jm3]);
         eFs += dmu[i] * dC[i];
       }
-      const float eFb = ex * P.force_x + ey * Fby - udFb;
+      const float eFb = exa * P.force_x + eya * Fby - udFb;
       const float ph = (dr - udr) * kCs2 * (G - w) + (eFs + eFb) * G;
       const float geq = w * p + rcs2 * (G - w) - 0.5f * ph;
       const float fneq = s.g[a][c2] - geq;
       s.g[a][c2] = fneq;
       s.eqf[a][q] = geq + ph;
-      Pxx += fneq * ex * ex;
-      Pyy += fneq * ey * ey;
-      Pxy += fneq * ex * ey;
+      Pxx += fneq * exa * exa;
+      Pyy += fneq * eya * eya;
+      Pxy += fneq * exa * eya;
       const float ep = dp - udp - eFs - eFb;
 #pragma unroll
       for (int i = 0; i < NH; ++i) {
@@ -289,11 +291,12 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffe
     }
     // strain rate with the previous tau (R23) and the new tau (Eq. 31-33, R4)
     const float tp = B.tau_in[k];
-    const float fac = 3.0f * (2.0f * tp / (2.0f * tp + 1.0f)) / (2.0f * tp * rcs2);
+    // (1/cs^2) (2 tau / (2 tau + 1)) / (2 tau rho cs^2) = 9 / ((2 tau + 1) rho)
+    const float fac = 9.0f * irho / (2.0f * tp + 1.0f);
     const float Dxx = -fac * Pxx, Dyy = -fac * Pyy, Dxy = -fac * Pxy;
     const float gd = sqrtf(2.0f * (Dxx * Dxx + Dyy * Dyy + 2.0f * Dxy * Dxy));
     const float C3 = 1.0f - Cc[0] - (NH == 2 ? Cc[NH - 1] : 0.f);
-    const float tau1 = P.powerlaw ? tau_powerlaw(P, gd, rho) : P.tau[0];
+    const float tau1 = P.powerlaw ? tau_powerlaw(P, gd, irho) : P.tau[0];
     const float tn = tau_mix(P, Cc[0], NH == 2 ? Cc[NH - 1] : 0.f, C3, tau1);
     const float om = 1.0f / (tn + 0.5f);
     // pass B: g* = g - om (g - g^eq) + forcing, over g in shared memory
@@ -328,20 +331,20 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffe
   }
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    int s1 = yc1 - c_ey[a] * S::W1 - c_ex[a];
-    int s2 = yc2 - c_ey[a] * S::W2 - c_ex[a];
+    int s1 = yc1 - ey(a) * S::W1 - ex(a);
+    int s2 = yc2 - ey(a) * S::W2 - ex(a);
     int b = a;
     if (!per) {
-      const int ys = y - c_ey[a];
+      const int ys = y - ey(a);
       if (ys < 0 || ys >= ny) {  // half-way bounce-back: the population left y in -e_a
         s1 = yc1;
         s2 = yc2;
-        b = c_opp[a];
+        b = opp(a);
       }
     }
     B.g_out[(long long)a * plane + ky] = s.g[b][s2];
-    const float euy = c_ex[a] * uxy + c_ey[a] * uyy;
-    const float Gy = c_w[a] * (1.0f + 3.0f * euy + 4.5f * euy * euy - 1.5f * uuy);
+    const float euy = ex(a) * uxy + ey(a) * uyy;
+    const float Gy = wt(a) * (1.0f + 3.0f * euy + 4.5f * euy * euy - 1.5f * uuy);
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
       const float hv = s.hs[i][b][s1] + svy[i] * Gy;
@@ -376,15 +379,51 @@ static cudaError_t launch_fused_t(const DevParams &P, const FusedBuffers &B, cud
   return cudaGetLastError();
 }
 
-// Tile 32 x 8 with 352 threads (11 warps; the 1-ring has 34 x 10 = 340 nodes).
-void launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s) {
-  if (P.collapse_h) {
-    if (P.nh == 1) launch_fused_t<32, 8, 1, false, 352, 3>(P, B, s);
-    else launch_fused_t<32, 8, 2, false, 352, 2>(P, B, s);
-  } else {
-    if (P.nh == 1) launch_fused_t<32, 8, 1, true, 352, 3>(P, B, s);
-    else launch_fused_t<32, 8, 2, true, 352, 2>(P, B, s);
+// Launch configurations the autotuner chooses from: output tile TX x TY,
+// threads per CTA (sized to one of the rings so that a heavy stage runs in a
+// single pass) and the minimum resident CTAs per SM passed to the compiler.
+template <int NH, bool STORE_H>
+struct VariantTable {
+  static constexpr int kCount = NH == 1 ? 4 : 2;
+  static const char *name(int v) {
+    static const char *n1[4] = {"32x8/352/3", "32x8/448/2", "32x16/640/2", "64x8/704/1"};
+    static const char *n2[2] = {"32x8/352/2", "32x8/448/2"};
+    return NH == 1 ? n1[v] : n2[v];
   }
+  static cudaError_t launch(int v, const DevParams &P, const FusedBuffers &B, cudaStream_t s) {
+    if constexpr (NH == 1) {
+      switch (v) {
+        case 1: return launch_fused_t<32, 8, NH, STORE_H, 448, 2>(P, B, s);
+        case 2: return launch_fused_t<32, 16, NH, STORE_H, 640, 2>(P, B, s);
+        case 3: return launch_fused_t<64, 8, NH, STORE_H, 704, 1>(P, B, s);
+        default: return launch_fused_t<32, 8, NH, STORE_H, 352, 3>(P, B, s);
+      }
+    } else {
+      switch (v) {
+        case 1: return launch_fused_t<32, 8, NH, STORE_H, 448, 2>(P, B, s);
+        default: return launch_fused_t<32, 8, NH, STORE_H, 352, 2>(P, B, s);
+      }
+    }
+  }
+};
+
+int fused_variant_count(const DevParams &P) {
+  return P.nh == 1 ? VariantTable<1, true>::kCount : VariantTable<2, true>::kCount;
+}
+
+const char *fused_variant_name(const DevParams &P, int v) {
+  if (v < 0 || v >= fused_variant_count(P)) v = 0;
+  return P.nh == 1 ? VariantTable<1, true>::name(v) : VariantTable<2, true>::name(v);
+}
+
+cudaError_t launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v) {
+  if (v < 0 || v >= fused_variant_count(P)) v = 0;
+  if (P.collapse_h) {
+    if (P.nh == 1) return VariantTable<1, false>::launch(v, P, B, s);
+    return VariantTable<2, false>::launch(v, P, B, s);
+  }
+  if (P.nh == 1) return VariantTable<1, true>::launch(v, P, B, s);
+  return VariantTable<2, true>::launch(v, P, B, s);
 }
 
 bool fused_supported(const DevParams &P) { return P.fd_scheme == 0; }

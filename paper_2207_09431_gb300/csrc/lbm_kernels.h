@@ -30,7 +30,10 @@ struct FusedBuffers {
 };
 
 bool fused_supported(const DevParams &P);
-void launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s);
+// Launch configurations of the fused step (tile, threads, CTAs per SM).
+int fused_variant_count(const DevParams &P);
+const char *fused_variant_name(const DevParams &P, int v);
+cudaError_t launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v);
 
 void launch_macros(const DevParams &P, const StepBuffers &B, cudaStream_t s);
 void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s);

@@ -54,7 +54,7 @@ __device__ void gather_gradients(const DevParams &P, const CReader &cr, const fl
   const long long k0 = node_index(P, x, y);
   float Cn[9][3], rn[9], pn[9];
   for (int a = 0; a < 9; ++a) {
-    long long k = shifted(P, x, y, c_ex[a], c_ey[a]);
+    long long k = shifted(P, x, y, ex(a), ey(a));
     cr.at(k, Cn[a]);
     rn[a] = rho_of(P, Cn[a][0], Cn[a][1], Cn[a][2]);
     pn[a] = pf[k];
@@ -64,8 +64,8 @@ __device__ void gather_gradients(const DevParams &P, const CReader &cr, const fl
     n.C[j] = Cn[0][j];
     float sx = 0.f, sy = 0.f;
     for (int a = 0; a < 9; ++a) {
-      sx += c_w[a] * c_ex[a] * Cn[a][j];
-      sy += c_w[a] * c_ey[a] * Cn[a][j];
+      sx += wt(a) * ex(a) * Cn[a][j];
+      sy += wt(a) * ey(a) * Cn[a][j];
     }
     n.gC[j][0] = 3.0f * sx;
     n.gC[j][1] = 3.0f * sy;
@@ -75,10 +75,10 @@ __device__ void gather_gradients(const DevParams &P, const CReader &cr, const fl
   {
     float sx = 0.f, sy = 0.f, qx = 0.f, qy = 0.f;
     for (int a = 0; a < 9; ++a) {
-      sx += c_w[a] * c_ex[a] * rn[a];
-      sy += c_w[a] * c_ey[a] * rn[a];
-      qx += c_w[a] * c_ex[a] * pn[a];
-      qy += c_w[a] * c_ey[a] * pn[a];
+      sx += wt(a) * ex(a) * rn[a];
+      sy += wt(a) * ey(a) * rn[a];
+      qx += wt(a) * ex(a) * pn[a];
+      qy += wt(a) * ey(a) * pn[a];
     }
     n.grho[0] = 3.0f * sx;
     n.grho[1] = 3.0f * sy;
@@ -86,10 +86,10 @@ __device__ void gather_gradients(const DevParams &P, const CReader &cr, const fl
     n.gp[1] = 3.0f * qy;
   }
   for (int a = 0; a < 9; ++a) {
-    const int o = c_opp[a];
+    const int o = opp(a);
     float C2e[3] = {0.f, 0.f, 0.f}, r2e = 0.f, p2e = 0.f;
     if (P.fd_scheme == 1) {
-      long long k2 = shifted(P, x, y, 2 * c_ex[a], 2 * c_ey[a]);
+      long long k2 = shifted(P, x, y, 2 * ex(a), 2 * ey(a));
       cr.at(k2, C2e);
       r2e = rho_of(P, C2e[0], C2e[1], C2e[2]);
       p2e = pf[k2];
@@ -105,8 +105,8 @@ __device__ __forceinline__ float phi_g(const NodeCtx &n, int a, float G) {
   float e_rho = n.drho[a] - (n.ux * n.grho[0] + n.uy * n.grho[1]);
   float e_Fs = n.mu[0] * n.dC[0][a] + n.mu[1] * n.dC[1][a] + n.mu[2] * n.dC[2][a] -
                (n.ux * n.Fs[0] + n.uy * n.Fs[1]);
-  float e_Fb = (c_ex[a] - n.ux) * n.Fb[0] + (c_ey[a] - n.uy) * n.Fb[1];
-  return e_rho * kCs2 * (G - c_w[a]) + (e_Fs + e_Fb) * G;
+  float e_Fb = (ex(a) - n.ux) * n.Fb[0] + (ey(a) - n.uy) * n.Fb[1];
+  return e_rho * kCs2 * (G - wt(a)) + (e_Fs + e_Fb) * G;
 }
 
 // Forcing of Eq. 18 for order parameter i, direction a.
@@ -115,7 +115,7 @@ __device__ __forceinline__ float phi_h(const NodeCtx &n, int i, int a, float G) 
   float e_p = n.dp[a] - (n.ux * n.gp[0] + n.uy * n.gp[1]);
   float e_Fs = n.mu[0] * n.dC[0][a] + n.mu[1] * n.dC[1][a] + n.mu[2] * n.dC[2][a] -
                (n.ux * n.Fs[0] + n.uy * n.Fs[1]);
-  float e_Fb = (c_ex[a] - n.ux) * n.Fb[0] + (c_ey[a] - n.uy) * n.Fb[1];
+  float e_Fb = (ex(a) - n.ux) * n.Fb[0] + (ey(a) - n.uy) * n.Fb[1];
   return (e_C - n.C[i] / (n.rho * kCs2) * (e_p - e_Fs - e_Fb)) * G;
 }
 
@@ -149,7 +149,7 @@ __global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float 
   CReader cr{Cf, P.plane, P.nh};
   float Cn[9][3], rn[9];
   for (int a = 0; a < 9; ++a) {
-    long long kk = shifted(P, x, y, c_ex[a], c_ey[a]);
+    long long kk = shifted(P, x, y, ex(a), ey(a));
     cr.at(kk, Cn[a]);
     rn[a] = rho_of(P, Cn[a][0], Cn[a][1], Cn[a][2]);
   }
@@ -159,9 +159,9 @@ __global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float 
     n.C[j] = Cn[0][j];
     float sx = 0.f, sy = 0.f, lp = 0.f;
     for (int a = 0; a < 9; ++a) {
-      sx += c_w[a] * c_ex[a] * Cn[a][j];
-      sy += c_w[a] * c_ey[a] * Cn[a][j];
-      lp += c_w[a] * (Cn[a][j] - Cn[0][j]);
+      sx += wt(a) * ex(a) * Cn[a][j];
+      sy += wt(a) * ey(a) * Cn[a][j];
+      lp += wt(a) * (Cn[a][j] - Cn[0][j]);
     }
     n.gC[j][0] = 3.0f * sx;
     n.gC[j][1] = 3.0f * sy;
@@ -171,8 +171,8 @@ __global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float 
   {
     float sx = 0.f, sy = 0.f;
     for (int a = 0; a < 9; ++a) {
-      sx += c_w[a] * c_ex[a] * rn[a];
-      sy += c_w[a] * c_ey[a] * rn[a];
+      sx += wt(a) * ex(a) * rn[a];
+      sy += wt(a) * ey(a) * rn[a];
     }
     n.grho[0] = 3.0f * sx;
     n.grho[1] = 3.0f * sy;
@@ -186,8 +186,8 @@ __global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float 
   for (int a = 0; a < 9; ++a) {
     ga[a] = g[(long long)a * P.plane + k];
     m0 += ga[a];
-    mx += c_ex[a] * ga[a];
-    my += c_ey[a] * ga[a];
+    mx += ex(a) * ga[a];
+    my += ey(a) * ga[a];
   }
   n.ux = (3.0f * mx + 0.5f * (n.Fs[0] + n.Fb[0])) / n.rho;
   n.uy = (3.0f * my + 0.5f * (n.Fs[1] + n.Fb[1])) / n.rho;
@@ -199,10 +199,10 @@ __global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float 
   if (!write_tau) return;
   // directional derivatives of rho and C (the g forcing has no p derivative)
   for (int a = 0; a < 9; ++a) {
-    const int o = c_opp[a];
+    const int o = opp(a);
     float C2e[3] = {0.f, 0.f, 0.f}, r2e = 0.f;
     if (P.fd_scheme == 1) {
-      cr.at(shifted(P, x, y, 2 * c_ex[a], 2 * c_ey[a]), C2e);
+      cr.at(shifted(P, x, y, 2 * ex(a), 2 * ey(a)), C2e);
       r2e = rho_of(P, C2e[0], C2e[1], C2e[2]);
     }
     for (int j = 0; j < 3; ++j) n.dC[j][a] = dir_deriv(P.fd_scheme, Cn[o][j], Cn[0][j], Cn[a][j], C2e[j]);
@@ -214,16 +214,16 @@ __global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float 
   float Pxx = 0.f, Pyy = 0.f, Pxy = 0.f;
   for (int a = 0; a < 9; ++a) {
     float G = gamma_a(a, n.ux, n.uy);
-    float geq = c_w[a] * n.p + n.rho * kCs2 * (G - c_w[a]) - 0.5f * phi_g(n, a, G);
+    float geq = wt(a) * n.p + n.rho * kCs2 * (G - wt(a)) - 0.5f * phi_g(n, a, G);
     float fneq = fac * (ga[a] - geq);
-    Pxx += fneq * (float)(c_ex[a] * c_ex[a]);
-    Pyy += fneq * (float)(c_ey[a] * c_ey[a]);
-    Pxy += fneq * (float)(c_ex[a] * c_ey[a]);
+    Pxx += fneq * (float)(ex(a) * ex(a));
+    Pyy += fneq * (float)(ey(a) * ey(a));
+    Pxy += fneq * (float)(ex(a) * ey(a));
   }
   const float den = 2.0f * tp * n.rho * kCs2;
   const float Dxx = -Pxx / den, Dyy = -Pyy / den, Dxy = -Pxy / den;
   const float gd = sqrtf(2.0f * (Dxx * Dxx + Dyy * Dyy + 2.0f * Dxy * Dxy));
-  const float tau1 = P.powerlaw ? tau_powerlaw(P, gd, n.rho) : P.tau[0];
+  const float tau1 = P.powerlaw ? tau_powerlaw(P, gd, 1.0f / n.rho) : P.tau[0];
   const float tn = tau_mix(P, n.C[0], n.C[1], n.C[2], tau1);
   tau_new[k] = tn;
   shear[k] = gd;
@@ -242,17 +242,17 @@ __global__ void k_sources(DevParams P, const float *__restrict__ Cf, const float
     float gcx = 0.f, gcy = 0.f, gmx = 0.f, gmy = 0.f, lm = 0.f;
     const float m0 = mi[k];
     for (int a = 0; a < 9; ++a) {
-      long long kk = shifted(P, x, y, c_ex[a], c_ey[a]);
+      long long kk = shifted(P, x, y, ex(a), ey(a));
       float cv = Ci[kk], mv = mi[kk];
-      gcx += c_w[a] * c_ex[a] * cv;
-      gcy += c_w[a] * c_ey[a] * cv;
-      gmx += c_w[a] * c_ex[a] * mv;
-      gmy += c_w[a] * c_ey[a] * mv;
-      lm += c_w[a] * (mv - m0);
+      gcx += wt(a) * ex(a) * cv;
+      gcy += wt(a) * ey(a) * cv;
+      gmx += wt(a) * ex(a) * mv;
+      gmy += wt(a) * ey(a) * mv;
+      lm += wt(a) * (mv - m0);
     }
     const float lapmu = 6.0f * lm;
     const float C = Ci[k];
-    const float D0s = P.D0 / P.Sig[i];
+    const float D0s = P.d0_sig[i];
     float s;
     if (P.mobility == 1) {
       s = D0s * C * (1.0f - C) * lapmu + D0s * (1.0f - 2.0f * C) * (3.0f * gcx * 3.0f * gmx + 3.0f * gcy * 3.0f * gmy);
@@ -290,16 +290,16 @@ __global__ void k_collide(DevParams P, const float *__restrict__ g, const float 
   for (int a = 0; a < 9; ++a) {
     const float G = gamma_a(a, n.ux, n.uy);
     const float pg = phi_g(n, a, G);
-    const float geq = c_w[a] * n.p + n.rho * kCs2 * (G - c_w[a]) - 0.5f * pg;
+    const float geq = wt(a) * n.p + n.rho * kCs2 * (G - wt(a)) - 0.5f * pg;
     const float gv = g[(long long)a * P.plane + k];
     const float gstar = gv - omega * (gv - geq) + pg;
     // destination
-    int dx = x + c_ex[a], dy = y + c_ey[a];
+    int dx = x + ex(a), dy = y + ey(a);
     int da = a;
     long long kd;
     if (!P.periodic_y && (dy < 0 || dy >= P.ny)) {
       kd = k;
-      da = c_opp[a];
+      da = opp(a);
     } else {
       kd = node_index(P, wrap_x(dx, P.nx), P.periodic_y ? wrap_y(dy, P.ny, 1) : dy);
     }
@@ -325,10 +325,10 @@ __global__ void k_init(DevParams P, const float *__restrict__ Cf, const float *_
   NodeCtx n;
   gather_gradients(P, cr, pf, x, y, n);
   float Cn[9][3], lapC[3];
-  for (int a = 0; a < 9; ++a) cr.at(shifted(P, x, y, c_ex[a], c_ey[a]), Cn[a]);
+  for (int a = 0; a < 9; ++a) cr.at(shifted(P, x, y, ex(a), ey(a)), Cn[a]);
   for (int j = 0; j < 3; ++j) {
     float lp = 0.f;
-    for (int a = 0; a < 9; ++a) lp += c_w[a] * (Cn[a][j] - Cn[0][j]);
+    for (int a = 0; a < 9; ++a) lp += wt(a) * (Cn[a][j] - Cn[0][j]);
     lapC[j] = 6.0f * lp;
   }
   chem_potentials(P, n.C, lapC, n.mu);
@@ -340,12 +340,12 @@ __global__ void k_init(DevParams P, const float *__restrict__ Cf, const float *_
   n.Fb[1] = -n.rho * P.gravity;
   for (int a = 0; a < 9; ++a) {
     const float G = gamma_a(a, n.ux, n.uy);
-    g[(long long)a * P.plane + k] = c_w[a] * n.p + n.rho * kCs2 * (G - c_w[a]) - 0.5f * phi_g(n, a, G);
+    g[(long long)a * P.plane + k] = wt(a) * n.p + n.rho * kCs2 * (G - wt(a)) - 0.5f * phi_g(n, a, G);
     if (h)
       for (int i = 0; i < P.nh; ++i)
         h[((long long)i * 9 + a) * P.plane + k] = n.C[i] * G - 0.5f * phi_h(n, i, a, G);
   }
-  const float tau1 = P.powerlaw ? tau_powerlaw(P, 0.0f, n.rho) : P.tau[0];
+  const float tau1 = P.powerlaw ? tau_powerlaw(P, 0.0f, 1.0f / n.rho) : P.tau[0];
   tau[k] = tau_mix(P, n.C[0], n.C[1], n.C[2], tau1);
 }
 

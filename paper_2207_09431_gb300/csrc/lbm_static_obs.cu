@@ -74,7 +74,7 @@ __global__ void k_obs_partial(DevParams P, const float *__restrict__ g, const fl
     const long long k = (long long)y * P.pitch + x;
     float Cn[9][3], rn[9];
     for (int a = 0; a < 9; ++a) {
-      const int xs = wrap_x(x + c_ex[a], P.nx), ys = wrap_y(y + c_ey[a], P.ny, P.periodic_y);
+      const int xs = wrap_x(x + ex(a), P.nx), ys = wrap_y(y + ey(a), P.ny, P.periodic_y);
       order_params(P, hc, collapse, (long long)ys * P.pitch + xs, Cn[a]);
       rn[a] = rho_of(P, Cn[a][0], Cn[a][1], Cn[a][2]);
     }
@@ -82,17 +82,17 @@ __global__ void k_obs_partial(DevParams P, const float *__restrict__ g, const fl
     for (int j = 0; j < 3; ++j) {
       float sx = 0.f, sy = 0.f, lp = 0.f;
       for (int a = 0; a < 9; ++a) {
-        sx += c_w[a] * c_ex[a] * Cn[a][j];
-        sy += c_w[a] * c_ey[a] * Cn[a][j];
-        lp += c_w[a] * (Cn[a][j] - Cn[0][j]);
+        sx += wt(a) * ex(a) * Cn[a][j];
+        sy += wt(a) * ey(a) * Cn[a][j];
+        lp += wt(a) * (Cn[a][j] - Cn[0][j]);
       }
       gx[j] = 3.0f * sx;
       gy[j] = 3.0f * sy;
       lap[j] = 6.0f * lp;
     }
     for (int a = 0; a < 9; ++a) {
-      rx += c_w[a] * c_ex[a] * rn[a];
-      ry += c_w[a] * c_ey[a] * rn[a];
+      rx += wt(a) * ex(a) * rn[a];
+      ry += wt(a) * ey(a) * rn[a];
     }
     chem_potentials(P, Cn[0], lap, mu);
     const float Fsx = mu[0] * gx[0] + mu[1] * gx[1] + mu[2] * gx[2];
@@ -101,8 +101,8 @@ __global__ void k_obs_partial(DevParams P, const float *__restrict__ g, const fl
     float mx = 0.f, my = 0.f;
     for (int a = 0; a < 9; ++a) {
       const float ga = g[(long long)a * P.plane + k];
-      mx += c_ex[a] * ga;
-      my += c_ey[a] * ga;
+      mx += ex(a) * ga;
+      my += ey(a) * ga;
     }
     const float ux = (3.0f * mx + 0.5f * (Fsx + P.force_x)) / rho;
     const float uy = (3.0f * my + 0.5f * (Fsy - rho * P.gravity)) / rho;
@@ -228,6 +228,12 @@ extern "C" lbm_status lbm_observables_static(const lbm_params *p, const float *g
   d.Sig[2] = (float)S3;
   d.SigT = (float)(3.0 / (1.0 / S1 + 1.0 / S2 + 1.0 / S3));
   d.xi = (float)p->xi;
+  const double Sg[3] = {S1, S2, S3};
+  for (int i = 0; i < 3; ++i) {
+    d.inv_sig[i] = (float)(1.0 / Sg[i]);
+    d.grad_coef[i] = (float)(0.75 * p->xi * Sg[i]);
+  }
+  d.mu_pre = (float)(4.0 * (3.0 / (1.0 / S1 + 1.0 / S2 + 1.0 / S3)) / p->xi);
   d.gravity = (float)p->gravity;
   d.force_x = (float)p->force_x;
   d.plane = plane_stride;

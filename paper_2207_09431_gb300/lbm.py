@@ -66,7 +66,8 @@ DEFAULTS = dict(periodic_y=0, rho=(1.0, 1.0, 1.0), tau=(0.5, 0.5, 0.5), powerlaw
 EXPORTED = ["lbm_version", "lbm_required_bytes", "lbm_create", "lbm_init_bubbles", "lbm_set_fields",
             "lbm_step", "lbm_observables", "lbm_get_field", "lbm_save", "lbm_load", "lbm_destroy",
             "lbm_last_error", "lbm_postprocess", "lbm_kernels_per_step", "lbm_kernel_name",
-            "lbm_profile_step", "lbm_observables_static"]
+            "lbm_profile_step", "lbm_observables_static", "lbm_autotune", "lbm_kernel_config_count",
+            "lbm_set_kernel_config"]
 
 
 def load_library(path: str | None = None):
@@ -100,6 +101,9 @@ def load_library(path: str | None = None):
     lib.lbm_kernel_name.argtypes = [vp, ctypes.c_int]
     lib.lbm_kernel_name.restype = ctypes.c_char_p
     lib.lbm_profile_step.argtypes = [vp, ctypes.c_longlong, d, ctypes.c_int]
+    lib.lbm_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+    lib.lbm_kernel_config_count.argtypes = [vp]
+    lib.lbm_set_kernel_config.argtypes = [vp, ctypes.c_int]
     lib.lbm_observables_static.argtypes = [P(lbm_params), vp, vp, ctypes.c_int, ctypes.c_longlong, d, vp]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
@@ -247,6 +251,20 @@ def lbm_profile_step(h, nsteps: int) -> dict:
     return {lbm_kernel_name(h, i): float(out[i]) for i in range(k)}
 
 
+def lbm_autotune(h, reps: int = 5) -> int:
+    chosen = ctypes.c_int(0)
+    _check(h, load_library().lbm_autotune(h, int(reps), ctypes.byref(chosen)), "lbm_autotune")
+    return int(chosen.value)
+
+
+def lbm_kernel_config_count(h) -> int:
+    return int(load_library().lbm_kernel_config_count(h))
+
+
+def lbm_set_kernel_config(h, config: int):
+    _check(h, load_library().lbm_set_kernel_config(h, int(config)), "lbm_set_kernel_config")
+
+
 def lbm_observables_static(params, g_ptr: int, hc_ptr: int, pitch: int, plane_stride: int,
                            stream_ptr: int = 0) -> np.ndarray:
     """Raw observable sums (15 doubles) of a state in caller-held device buffers;
@@ -304,6 +322,11 @@ class Lattice:
     def kernel_times(self, reps=5) -> dict:
         """Mean device ms of each kernel of the step (advances `reps` steps)."""
         return lbm_profile_step(self.h, reps)
+
+    def autotune(self, reps=5) -> str:
+        """Picks the fastest launch configuration; returns the kernel's name."""
+        lbm_autotune(self.h, reps)
+        return lbm_kernel_name(self.h, 0)
 
     def launches_per_step(self) -> int:
         return lbm_kernels_per_step(self.h)

@@ -200,6 +200,35 @@ def test_collapsed_state_form(lbm, mobility):
         c.lat.field("h")
 
 
+@pytest.mark.parametrize("ncomp,collapse", [(2, 0), (2, 1), (3, 0)])
+def test_every_kernel_config_gives_the_same_fields(lbm, ncomp, collapse):
+    """The autotuner may pick any launch configuration: all of them compute the
+    same node values (tile shapes only change which CTA computes a node)."""
+    if ncomp == 2:
+        p, C = _bubble_case(70, 50, mobility=1)
+    else:
+        p, b = inputs.three_comp_case(nx=64, mobility=1, seed=5)
+        p = dict(p, nx=66, ny=54)
+        b = [(cx * 66 / 64, cy * 54 / 64, R, c) for (cx, cy, R, c) in b]
+        C = inputs.round_to_fp32(inputs.bubble_fields(66, 54, 3, p["xi"], b, seed=5, noise=1e-8, periodic_y=True))
+    p = dict(p, collapse_h=collapse)
+    ref = None
+    lat0 = lbm.Lattice(p)
+    n = lbm.lbm_kernel_config_count(lat0.h)
+    assert n >= 2
+    for v in range(n):
+        lat = lbm.Lattice(p)
+        lbm.lbm_set_kernel_config(lat.h, v)
+        lat.set_fields(C)
+        lat.step(25)
+        got = {f: lat.field(f) for f in ("C1", "p", "uy", "tau", "g")}
+        if ref is None:
+            ref = got
+            continue
+        for f in got:
+            assert relerr(got[f], ref[f]) <= 1e-6, (v, f)
+
+
 def test_full_size_windows(lbm):
     """Bench workload (2048 x 4096 rising bubble, density ratio 1000) in the
     launch configuration the benchmark times: after two steps, nodes at least
