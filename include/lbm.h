@@ -191,6 +191,35 @@ const char *lbm_last_error(const lbm_handle *h);
  * left at 0. */
 lbm_status lbm_postprocess(const lbm_params *p, const double raw[15], lbm_obs *out);
 
+/* ---- Batched ensembles ------------------------------------------------------
+ * Many lattices (cases) with their own size and parameters advance together:
+ * one kernel launch per time step covers every tile of every active case
+ * (a work list of (case, tile) items), and runs of 16 steps are replayed from a
+ * captured CUDA graph.  All cases share ncomp and collapse_h and use
+ * fd_scheme 0.  Each case is an ordinary handle carved from the batch arena:
+ * set its initial state, read its observables, fields and checkpoints with the
+ * single-lattice calls on lbm_batch_case(b, i); lbm_step on a case advances that
+ * case alone.  The arena (>= lbm_batch_required_bytes) and the stream stay the
+ * caller's, as for lbm_create. */
+typedef struct lbm_batch lbm_batch;
+
+size_t lbm_batch_required_bytes(const lbm_params *cases, int ncases);
+lbm_status lbm_batch_create(const lbm_params *cases, int ncases, void *dev_arena, size_t arena_bytes,
+                            void *cuda_stream, lbm_batch **out);
+/* The handle of case i (owned by the batch; NULL if i is out of range). */
+lbm_handle *lbm_batch_case(lbm_batch *b, int i);
+/* Includes (1) or excludes (0) case i from lbm_batch_step (e.g. once it reached
+ * its terminal velocity).  Cases start active. */
+lbm_status lbm_batch_set_active(lbm_batch *b, int i, int active);
+/* Advances every active case with an initial state by nsteps and waits.  A
+ * case that produced a non-finite value is deactivated and the call returns
+ * LBM_E_DIVERGED naming it in lbm_batch_last_error; the others advanced. */
+lbm_status lbm_batch_step(lbm_batch *b, long long nsteps);
+/* As lbm_autotune, over the whole work list; states are not advanced. */
+lbm_status lbm_batch_autotune(lbm_batch *b, int reps, int *chosen);
+void lbm_batch_destroy(lbm_batch *b);
+const char *lbm_batch_last_error(const lbm_batch *b);
+
 /* Largest lattice (nx * ny nodes) lbm_observables_static accepts. */
 #define LBM_STATIC_MAX_NODES (1 << 20)
 

@@ -1,0 +1,261 @@
+// Batched ensemble of lattices (many rising-bubble cases of different sizes
+// and parameters): every active case advances in one kernel launch per time
+// step over a work list of (case, tile) items, and runs of steps are replayed
+// from a captured CUDA graph.  Each case is an ordinary lbm_handle carved from
+// the batch arena, so initial conditions, observables, fields and checkpoints
+// use the single-lattice calls on lbm_batch_case(b, i).
+#include <cuda_runtime.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace {
+
+constexpr int kGraphSteps = 16;  // time steps per captured graph (even: parity returns)
+
+size_t batch_table_bytes(int n) { return align_up((size_t)n * sizeof(lbm::BatchCase), kAlign); }
+size_t batch_err_bytes(int n) { return align_up((size_t)n * sizeof(unsigned), kAlign); }
+
+// Upper bound of work items: tiles of the smallest tile shape.
+size_t max_work(const lbm_params *cases, int n) {
+  size_t w = 0;
+  for (int i = 0; i < n; ++i) w += (size_t)((cases[i].nx + 31) / 32) * ((cases[i].ny + 7) / 8);
+  return w;
+}
+
+}  // namespace
+
+struct lbm_batch {
+  int n = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<lbm_handle *> h;
+  std::vector<char> active;
+  lbm::BatchCase *d_cases = nullptr;
+  lbm::WorkItem *d_work = nullptr;
+  unsigned *d_err = nullptr;
+  size_t work_cap = 0;
+  int nwork = 0;
+  int variant = 0;
+  int nh = 1;
+  bool collapse = false;
+  bool work_valid = false;
+  cudaGraphExec_t graph = nullptr;
+  int graph_nwork = -1, graph_variant = -1;
+  std::string last_error;
+
+  lbm_status fail(lbm_status s, const std::string &m) {
+    last_error = m;
+    return s;
+  }
+  lbm_status cuda_fail(cudaError_t e, const char *where) {
+    last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return LBM_E_CUDA;
+  }
+  ~lbm_batch() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (auto *x : h) delete x;
+  }
+
+  // Work list of the active, initialised cases for tile variant v; uploads it.
+  cudaError_t build_work(int v, int *count) {
+    std::vector<lbm::WorkItem> w;
+    for (int i = 0; i < n; ++i) {
+      if (!active[i] || !h[i]->initialized) continue;
+      int tx = 32, ty = 8;
+      lbm::fused_variant_tile(h[i]->dp, v, &tx, &ty);
+      for (int y0 = 0; y0 < h[i]->dp.ny; y0 += ty)
+        for (int x0 = 0; x0 < h[i]->dp.nx; x0 += tx) w.push_back({i, x0, y0});
+    }
+    *count = (int)w.size();
+    if (w.empty()) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(d_work, w.data(), w.size() * sizeof(lbm::WorkItem), cudaMemcpyHostToDevice,
+                                    stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    return e;
+  }
+
+  // Case table with every case's parameters, both buffer sets and current parity.
+  cudaError_t upload_table() {
+    std::vector<lbm::BatchCase> t(n);
+    for (int i = 0; i < n; ++i) {
+      t[i].P = h[i]->dp;
+      t[i].B[0] = h[i]->fused_buffers(0, false);
+      t[i].B[1] = h[i]->fused_buffers(1, false);
+      t[i].B[0].err = t[i].B[1].err = d_err + i;
+      t[i].base_parity = h[i]->cur;
+    }
+    cudaError_t e = cudaMemcpyAsync(d_cases, t.data(), t.size() * sizeof(lbm::BatchCase), cudaMemcpyHostToDevice,
+                                    stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    return e;
+  }
+};
+
+extern "C" {
+
+size_t lbm_batch_required_bytes(const lbm_params *cases, int ncases) {
+  if (!cases || ncases < 1) return 0;
+  size_t total = 0;
+  for (int i = 0; i < ncases; ++i) {
+    const size_t b = lbm_required_bytes(&cases[i]);
+    if (b == 0) return 0;
+    total += align_up(b, kAlign);
+  }
+  total += batch_table_bytes(ncases) + batch_err_bytes(ncases);
+  total += align_up(max_work(cases, ncases) * sizeof(lbm::WorkItem), kAlign);
+  return total;
+}
+
+lbm_status lbm_batch_create(const lbm_params *cases, int ncases, void *dev_arena, size_t arena_bytes,
+                            void *cuda_stream, lbm_batch **out) {
+  if (!out) return LBM_E_INVAL;
+  *out = nullptr;
+  const size_t need = lbm_batch_required_bytes(cases, ncases);
+  if (need == 0) return LBM_E_INVAL;
+  if (!dev_arena || ((uintptr_t)dev_arena % kAlign) != 0) return LBM_E_INVAL;
+  if (arena_bytes < need) return LBM_E_NOMEM;
+  for (int i = 0; i < ncases; ++i) {
+    if (cases[i].ncomp != cases[0].ncomp || cases[i].collapse_h != cases[0].collapse_h || cases[i].fd_scheme != 0)
+      return LBM_E_INVAL;  // one kernel: same component count and state form, central differences
+  }
+  lbm_batch *b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_E_NOMEM;
+  b->n = ncases;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->nh = cases[0].ncomp - 1;
+  b->collapse = cases[0].collapse_h != 0;
+  b->active.assign(ncases, 1);
+  char *base = (char *)dev_arena;
+  size_t off = 0;
+  for (int i = 0; i < ncases; ++i) {
+    const size_t bytes = align_up(lbm_required_bytes(&cases[i]), kAlign);
+    lbm_handle *hi = nullptr;
+    lbm_status st = lbm_create(&cases[i], base + off, bytes, cuda_stream, &hi);
+    if (st != LBM_OK) {
+      delete b;
+      return st;
+    }
+    b->h.push_back(hi);
+    off += bytes;
+  }
+  b->d_cases = (lbm::BatchCase *)(base + off);
+  off += batch_table_bytes(ncases);
+  b->d_err = (unsigned *)(base + off);
+  off += batch_err_bytes(ncases);
+  b->d_work = (lbm::WorkItem *)(base + off);
+  b->work_cap = max_work(cases, ncases);
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_handle *lbm_batch_case(lbm_batch *b, int i) { return (b && i >= 0 && i < b->n) ? b->h[i] : nullptr; }
+
+lbm_status lbm_batch_set_active(lbm_batch *b, int i, int active) {
+  if (!b || i < 0 || i >= b->n) return LBM_E_INVAL;
+  b->active[i] = active ? 1 : 0;
+  b->work_valid = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch *b, int reps, int *chosen) {
+  if (!b || reps < 1) return LBM_E_INVAL;
+  cudaError_t e = b->upload_table();
+  if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_autotune table");
+  const int nv = lbm::fused_variant_count(b->h[0]->dp);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return b->fail(LBM_E_CUDA, "cudaEventCreate");
+  int best = 0;
+  float best_ms = 0.f;
+  for (int v = 0; v < nv && e == cudaSuccess; ++v) {
+    int nw = 0;
+    e = b->build_work(v, &nw);
+    if (e != cudaSuccess || nw == 0) break;
+    // parity 0 reads every case's current state and writes its spare buffers
+    e = lbm::launch_batched_step(b->nh, b->collapse, b->d_cases, b->d_work, nw, 0, b->stream, v);
+    if (e != cudaSuccess) break;
+    cudaEventRecord(e0, b->stream);
+    for (int r = 0; r < reps; ++r) lbm::launch_batched_step(b->nh, b->collapse, b->d_cases, b->d_work, nw, 0, b->stream, v);
+    cudaEventRecord(e1, b->stream);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && (v == 0 || ms < best_ms)) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_autotune");
+  b->variant = best;
+  b->work_valid = false;
+  if (chosen) *chosen = best;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch *b, long long nsteps) {
+  if (!b || nsteps < 0) return LBM_E_INVAL;
+  if (nsteps == 0) return LBM_OK;
+  cudaError_t e = cudaSuccess;
+  if (!b->work_valid) {
+    e = b->build_work(b->variant, &b->nwork);
+    if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step work list");
+    b->work_valid = true;
+  }
+  if (b->nwork == 0) return b->fail(LBM_E_STATE, "no active, initialised case");
+  e = b->upload_table();
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, (size_t)b->n * sizeof(unsigned), b->stream);
+  if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step table");
+  const long long graphs = nsteps / kGraphSteps;
+  if (graphs > 0 && (!b->graph || b->graph_nwork != b->nwork || b->graph_variant != b->variant)) {
+    // kernel attributes are set outside the capture
+    e = lbm::launch_batched_step(b->nh, b->collapse, b->d_cases, b->d_work, 0, 0, b->stream, b->variant);
+    if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step prepare");
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t)
+      e = lbm::launch_batched_step(b->nh, b->collapse, b->d_cases, b->d_work, b->nwork, t & 1, b->stream, b->variant);
+    cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = ec;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step graph capture");
+    b->graph_nwork = b->nwork;
+    b->graph_variant = b->variant;
+  }
+  for (long long r = 0; r < graphs && e == cudaSuccess; ++r) e = cudaGraphLaunch(b->graph, b->stream);
+  for (long long t = graphs * kGraphSteps; t < nsteps && e == cudaSuccess; ++t)
+    e = lbm::launch_batched_step(b->nh, b->collapse, b->d_cases, b->d_work, b->nwork, (int)(t & 1), b->stream,
+                                 b->variant);
+  if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step launch");
+  std::vector<unsigned> err(b->n);
+  e = cudaMemcpyAsync(err.data(), b->d_err, err.size() * sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step");
+  std::string diverged;
+  for (int i = 0; i < b->n; ++i) {
+    if (!b->active[i] || !b->h[i]->initialized) continue;
+    if (nsteps & 1) b->h[i]->cur = 1 - b->h[i]->cur;
+    b->h[i]->step += nsteps;
+    if (err[i]) {
+      diverged += " " + std::to_string(i);
+      b->active[i] = 0;
+      b->work_valid = false;
+    }
+  }
+  if (!diverged.empty()) return b->fail(LBM_E_DIVERGED, "non-finite values in case(s)" + diverged + "; deactivated");
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b) { delete b; }
+
+const char *lbm_batch_last_error(const lbm_batch *b) { return b ? b->last_error.c_str() : "NULL batch"; }
+
+}  // extern "C"

@@ -81,13 +81,11 @@ __device__ __forceinline__ int i1(int lx, int ly) { return (ly + 1) * (TX + 2) +
 // of the FP32 sums) at 88 instead of 152 bytes per node-step.
 // NT threads per CTA (NT >= TX * TY); NT close to the size of R1 lets the
 // heaviest stage run in one pass.
-template <int TX, int TY, int NH, bool STORE_H, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffers B) {
+template <int TX, int TY, int NH, bool STORE_H, int NT>
+__device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffers &B, int x0, int y0,
+                                           Smem<TX, TY, NH> &s) {
   using S = Smem<TX, TY, NH>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S &s = *reinterpret_cast<S *>(smem_raw);
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const long long plane = P.plane;
   const int nx = P.nx, ny = P.ny, per = P.periodic_y, pitch = P.pitch;
 
@@ -361,6 +359,32 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffe
   }
 }
 
+// One lattice: tile (blockIdx.x, blockIdx.y).
+template <int TX, int TY, int NH, bool STORE_H, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffers B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fused_tile<TX, TY, NH, STORE_H, NT>(P, B, blockIdx.x * TX, blockIdx.y * TY,
+                                      *reinterpret_cast<Smem<TX, TY, NH> *>(smem_raw));
+}
+
+// Many lattices in one launch: CTA b takes work item b = (case, tile origin);
+// the case's parameters and buffers are staged in shared memory.  parity
+// selects which of the case's two buffer sets is the input this step.
+template <int TX, int TY, int NH, bool STORE_H, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_step_batched(const BatchCase *__restrict__ cases,
+                                                           const WorkItem *__restrict__ work, int parity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ DevParams sP;
+  __shared__ FusedBuffers sB;
+  const WorkItem w = work[blockIdx.x];
+  if (threadIdx.x == 0) {
+    sP = cases[w.case_id].P;
+    sB = cases[w.case_id].B[cases[w.case_id].base_parity ^ parity];
+  }
+  __syncthreads();
+  fused_tile<TX, TY, NH, STORE_H, NT>(sP, sB, w.x0, w.y0, *reinterpret_cast<Smem<TX, TY, NH> *>(smem_raw));
+}
+
 // ---------------------------------------------------------------- launcher
 
 template <int TX, int TY, int NH, bool STORE_H, int NT, int MINB>
@@ -379,6 +403,24 @@ static cudaError_t launch_fused_t(const DevParams &P, const FusedBuffers &B, cud
   return cudaGetLastError();
 }
 
+// nwork == 0 only sets the kernel's shared-memory attribute (done before any
+// stream capture).
+template <int TX, int TY, int NH, bool STORE_H, int NT, int MINB>
+static cudaError_t launch_batched_t(const BatchCase *cases, const WorkItem *work, int nwork, int parity,
+                                   cudaStream_t s) {
+  const size_t smem = sizeof(Smem<TX, TY, NH>);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_batched<TX, TY, NH, STORE_H, NT, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (nwork <= 0) return cudaSuccess;
+  k_step_batched<TX, TY, NH, STORE_H, NT, MINB><<<nwork, NT, smem, s>>>(cases, work, parity);
+  return cudaGetLastError();
+}
+
 // Launch configurations the autotuner chooses from: output tile TX x TY,
 // threads per CTA (sized to one of the rings so that a heavy stage runs in a
 // single pass) and the minimum resident CTAs per SM passed to the compiler.
@@ -389,6 +431,27 @@ struct VariantTable {
     static const char *n1[4] = {"32x8/352/3", "32x8/448/2", "32x16/640/2", "64x8/704/1"};
     static const char *n2[2] = {"32x8/352/2", "32x8/448/2"};
     return NH == 1 ? n1[v] : n2[v];
+  }
+  static void tile(int v, int *tx, int *ty) {
+    static const int t1[4][2] = {{32, 8}, {32, 8}, {32, 16}, {64, 8}};
+    *tx = t1[NH == 1 ? v : 0][0];
+    *ty = t1[NH == 1 ? v : 0][1];
+  }
+  static cudaError_t launch_batched(int v, const BatchCase *c, const WorkItem *w, int n, int parity,
+                                    cudaStream_t s) {
+    if constexpr (NH == 1) {
+      switch (v) {
+        case 1: return launch_batched_t<32, 8, NH, STORE_H, 448, 2>(c, w, n, parity, s);
+        case 2: return launch_batched_t<32, 16, NH, STORE_H, 640, 2>(c, w, n, parity, s);
+        case 3: return launch_batched_t<64, 8, NH, STORE_H, 704, 1>(c, w, n, parity, s);
+        default: return launch_batched_t<32, 8, NH, STORE_H, 352, 3>(c, w, n, parity, s);
+      }
+    } else {
+      switch (v) {
+        case 1: return launch_batched_t<32, 8, NH, STORE_H, 448, 2>(c, w, n, parity, s);
+        default: return launch_batched_t<32, 8, NH, STORE_H, 352, 2>(c, w, n, parity, s);
+      }
+    }
   }
   static cudaError_t launch(int v, const DevParams &P, const FusedBuffers &B, cudaStream_t s) {
     if constexpr (NH == 1) {
@@ -424,6 +487,24 @@ cudaError_t launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStr
   }
   if (P.nh == 1) return VariantTable<1, true>::launch(v, P, B, s);
   return VariantTable<2, true>::launch(v, P, B, s);
+}
+
+void fused_variant_tile(const DevParams &P, int v, int *tx, int *ty) {
+  if (v < 0 || v >= fused_variant_count(P)) v = 0;
+  if (P.nh == 1) VariantTable<1, true>::tile(v, tx, ty);
+  else VariantTable<2, true>::tile(v, tx, ty);
+}
+
+cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+                                int parity, cudaStream_t s, int v) {
+  const int count = nh == 1 ? VariantTable<1, true>::kCount : VariantTable<2, true>::kCount;
+  if (v < 0 || v >= count) v = 0;
+  if (collapse_h) {
+    if (nh == 1) return VariantTable<1, false>::launch_batched(v, cases, work, nwork, parity, s);
+    return VariantTable<2, false>::launch_batched(v, cases, work, nwork, parity, s);
+  }
+  if (nh == 1) return VariantTable<1, true>::launch_batched(v, cases, work, nwork, parity, s);
+  return VariantTable<2, true>::launch_batched(v, cases, work, nwork, parity, s);
 }
 
 bool fused_supported(const DevParams &P) { return P.fd_scheme == 0; }

@@ -29,7 +29,22 @@ struct FusedBuffers {
   unsigned *err;
 };
 
+// One lattice of a batch: its parameters and both buffer sets; buffer set
+// base_parity ^ parity is the input of the step launched with `parity`.
+struct BatchCase {
+  DevParams P;
+  FusedBuffers B[2];
+  int base_parity;
+};
+// One CTA of a batched step: a case and the origin of one of its tiles.
+struct WorkItem {
+  int case_id, x0, y0;
+};
+
 bool fused_supported(const DevParams &P);
+void fused_variant_tile(const DevParams &P, int v, int *tx, int *ty);
+cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+                                int parity, cudaStream_t s, int v);
 // Launch configurations of the fused step (tile, threads, CTAs per SM).
 int fused_variant_count(const DevParams &P);
 const char *fused_variant_name(const DevParams &P, int v);

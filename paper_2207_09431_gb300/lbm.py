@@ -67,7 +67,9 @@ EXPORTED = ["lbm_version", "lbm_required_bytes", "lbm_create", "lbm_init_bubbles
             "lbm_step", "lbm_observables", "lbm_get_field", "lbm_save", "lbm_load", "lbm_destroy",
             "lbm_last_error", "lbm_postprocess", "lbm_kernels_per_step", "lbm_kernel_name",
             "lbm_profile_step", "lbm_observables_static", "lbm_autotune", "lbm_kernel_config_count",
-            "lbm_set_kernel_config"]
+            "lbm_set_kernel_config", "lbm_batch_required_bytes", "lbm_batch_create", "lbm_batch_case",
+            "lbm_batch_set_active", "lbm_batch_step", "lbm_batch_autotune", "lbm_batch_destroy",
+            "lbm_batch_last_error"]
 
 
 def load_library(path: str | None = None):
@@ -104,6 +106,18 @@ def load_library(path: str | None = None):
     lib.lbm_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
     lib.lbm_kernel_config_count.argtypes = [vp]
     lib.lbm_set_kernel_config.argtypes = [vp, ctypes.c_int]
+    lib.lbm_batch_required_bytes.restype = ctypes.c_size_t
+    lib.lbm_batch_required_bytes.argtypes = [P(lbm_params), ctypes.c_int]
+    lib.lbm_batch_create.argtypes = [P(lbm_params), ctypes.c_int, vp, ctypes.c_size_t, vp, P(vp)]
+    lib.lbm_batch_case.restype = vp
+    lib.lbm_batch_case.argtypes = [vp, ctypes.c_int]
+    lib.lbm_batch_set_active.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.lbm_batch_step.argtypes = [vp, ctypes.c_longlong]
+    lib.lbm_batch_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+    lib.lbm_batch_destroy.argtypes = [vp]
+    lib.lbm_batch_destroy.restype = None
+    lib.lbm_batch_last_error.argtypes = [vp]
+    lib.lbm_batch_last_error.restype = ctypes.c_char_p
     lib.lbm_observables_static.argtypes = [P(lbm_params), vp, vp, ctypes.c_int, ctypes.c_longlong, d, vp]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
@@ -276,6 +290,118 @@ def lbm_observables_static(params, g_ptr: int, hc_ptr: int, pitch: int, plane_st
                                                ctypes.c_void_p(stream_ptr))
     _check(None, rc, "lbm_observables_static")
     return out
+
+
+def _check_batch(b, rc, what):
+    if rc != 0:
+        raise LbmError(rc, f"{what}: {load_library().lbm_batch_last_error(b).decode()}")
+
+
+def lbm_batch_required_bytes(cases) -> int:
+    arr = (lbm_params * len(cases))(*[c if isinstance(c, lbm_params) else make_params(c) for c in cases])
+    return int(load_library().lbm_batch_required_bytes(arr, len(cases)))
+
+
+def lbm_batch_create(cases, arena_ptr: int, arena_bytes: int, stream_ptr: int):
+    arr = (lbm_params * len(cases))(*[c if isinstance(c, lbm_params) else make_params(c) for c in cases])
+    b = ctypes.c_void_p()
+    rc = load_library().lbm_batch_create(arr, len(cases), ctypes.c_void_p(arena_ptr), arena_bytes,
+                                         ctypes.c_void_p(stream_ptr), ctypes.byref(b))
+    _check(None, rc, "lbm_batch_create")
+    return b
+
+
+def lbm_batch_case(b, i: int):
+    return ctypes.c_void_p(load_library().lbm_batch_case(b, int(i)))
+
+
+def lbm_batch_set_active(b, i: int, active: bool):
+    _check_batch(b, load_library().lbm_batch_set_active(b, int(i), int(bool(active))), "lbm_batch_set_active")
+
+
+def lbm_batch_step(b, nsteps: int):
+    _check_batch(b, load_library().lbm_batch_step(b, int(nsteps)), "lbm_batch_step")
+
+
+def lbm_batch_autotune(b, reps: int = 3) -> int:
+    chosen = ctypes.c_int(0)
+    _check_batch(b, load_library().lbm_batch_autotune(b, int(reps), ctypes.byref(chosen)), "lbm_batch_autotune")
+    return int(chosen.value)
+
+
+def lbm_batch_destroy(b):
+    if b:
+        load_library().lbm_batch_destroy(b)
+
+
+def lbm_batch_last_error(b) -> str:
+    return load_library().lbm_batch_last_error(b).decode()
+
+
+class Batch:
+    """Cases advancing together in one launch per step; `case(i)` gives a view
+    with the single-lattice methods (init, fields, observables)."""
+
+    def __init__(self, cases, device="cuda", stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU path exists)")
+        self.params = []
+        for c in cases:
+            full = dict(DEFAULTS)
+            full.update(c)
+            self.params.append(full)
+        prs = [make_params(c) for c in self.params]
+        self.nbytes = lbm_batch_required_bytes(prs)
+        if self.nbytes == 0:
+            raise LbmError(-1, "invalid batch parameters")
+        self.arena = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.arena.device)
+        self.b = lbm_batch_create(prs, self.arena.data_ptr(), self.nbytes, self.stream.cuda_stream)
+
+    def __del__(self):
+        b = getattr(self, "b", None)
+        if b:
+            lbm_batch_destroy(b)
+            self.b = None
+
+    def __len__(self):
+        return len(self.params)
+
+    def case(self, i) -> "CaseView":
+        return CaseView(self, i)
+
+    def step(self, nsteps):
+        lbm_batch_step(self.b, nsteps)
+
+    def set_active(self, i, active):
+        lbm_batch_set_active(self.b, i, active)
+
+    def autotune(self, reps=3) -> int:
+        return lbm_batch_autotune(self.b, reps)
+
+
+class CaseView:
+    """Single-lattice calls on case i of a Batch (the batch owns the handle)."""
+
+    def __init__(self, batch, i):
+        self._batch = batch
+        self.h = lbm_batch_case(batch.b, i)
+        p = batch.params[i]
+        self.nx, self.ny, self.nh = int(p["nx"]), int(p["ny"]), int(p["ncomp"]) - 1
+
+    def init_bubbles(self, bubbles, seed=0, noise=0.0):
+        lbm_init_bubbles(self.h, bubbles, seed, noise)
+
+    def set_fields(self, C, p=None, ux=None, uy=None):
+        lbm_set_fields(self.h, C, p, ux, uy)
+
+    def observables(self) -> dict:
+        return lbm_observables(self.h)
+
+    def field(self, name) -> np.ndarray:
+        return lbm_get_field(self.h, name, self.nx, self.ny, self.nh)
 
 
 class Lattice:
