@@ -195,7 +195,8 @@ lbm_status lbm_postprocess(const lbm_params *p, const double raw[15], lbm_obs *o
  * Many lattices (cases) with their own size and parameters advance together:
  * one kernel launch per time step covers every tile of every active case
  * (a work list of (case, tile) items), and runs of 16 steps are replayed from a
- * captured CUDA graph.  All cases share ncomp and collapse_h and use
+ * captured CUDA graph (on a created stream; on the legacy or per-thread default
+ * stream the steps are launched directly).  All cases share ncomp and collapse_h and use
  * fd_scheme 0.  Each case is an ordinary handle carved from the batch arena:
  * set its initial state, read its observables, fields and checkpoints with the
  * single-lattice calls on lbm_batch_case(b, i); lbm_step on a case advances that
@@ -219,6 +220,42 @@ lbm_status lbm_batch_step(lbm_batch *b, long long nsteps);
 lbm_status lbm_batch_autotune(lbm_batch *b, int reps, int *chosen);
 void lbm_batch_destroy(lbm_batch *b);
 const char *lbm_batch_last_error(const lbm_batch *b);
+
+/* ---- Surrogate network ------------------------------------------------------
+ * MLP 5 -> 128 -> 128 -> 128 -> 2 (tanh hidden layers) from (n, Eo, log10 Mo,
+ * density ratio, viscosity ratio) to (log terminal velocity, log drag
+ * coefficient), BF16 weights and FP32 accumulation on the tensor cores, an
+ * ensemble of `members` networks trained with Adam on the caller's lattice
+ * Boltzmann results.  Parameters per member: surr_param_count() floats, layer
+ * by layer W (out x in, row-major) then b.  The arena (>= surr_required_bytes)
+ * and stream stay the caller's.  The paper has no surrogate; it serves the
+ * parameter studies of Sec. 4. */
+typedef struct surr_net surr_net;
+
+int surr_param_count(void);
+size_t surr_required_bytes(int members, int max_batch, int max_rows);
+/* init_weights: members x surr_param_count() doubles (host). */
+lbm_status surr_create(int members, int max_batch, int max_rows, const double *init_weights, void *dev_arena,
+                       size_t arena_bytes, void *cuda_stream, surr_net **out);
+void surr_destroy(surr_net *n);
+const char *surr_last_error(const surr_net *n);
+/* Current FP32 master weights of one member (surr_param_count() doubles). */
+lbm_status surr_get_weights(surr_net *n, int member, double *out);
+/* The raw network of one member on rows x 5 inputs (no normalisation): outputs
+ * Y (rows x 2, may be NULL); with targets T (rows x 2) also the loss
+ * (1/2B) sum (y - t)^2 and its gradients (may be NULL). */
+lbm_status surr_forward_backward(surr_net *n, int member, const double *X, const double *T, int rows, double *Y,
+                                 double *loss, double *grads);
+/* Trains every member: inputs and targets are normalised per column with this
+ * set's mean and standard deviation, `epochs` passes of mini-batches of size
+ * `batch` (shuffled with `seed`; batch >= rows: one full-batch step per epoch in
+ * the given order), Adam with rate lr.  The input box of the set is kept as the
+ * training hull.  final_loss (may be NULL): loss of the last mini-batch. */
+lbm_status surr_train(surr_net *n, const double *X, const double *Y, int rows, int epochs, int batch, double lr,
+                      unsigned long long seed, double *final_loss);
+/* Ensemble mean and spread (max - min) of the two outputs for rows x 5 raw
+ * inputs; outside[r] = 1 when input r lies outside the training box. */
+lbm_status surr_predict(surr_net *n, const double *X, int rows, double *y_mean, double *y_spread, int *outside);
 
 /* Largest lattice (nx * ny nodes) lbm_observables_static accepts. */
 #define LBM_STATIC_MAX_NODES (1 << 20)

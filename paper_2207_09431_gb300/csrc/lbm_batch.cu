@@ -211,7 +211,9 @@ lbm_status lbm_batch_step(lbm_batch *b, long long nsteps) {
   e = b->upload_table();
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, (size_t)b->n * sizeof(unsigned), b->stream);
   if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step table");
-  const long long graphs = nsteps / kGraphSteps;
+  // graphs need a capturable stream: not the legacy or per-thread default stream
+  const bool capturable = b->stream != nullptr && b->stream != cudaStreamLegacy && b->stream != cudaStreamPerThread;
+  const long long graphs = capturable ? nsteps / kGraphSteps : 0;
   if (graphs > 0 && (!b->graph || b->graph_nwork != b->nwork || b->graph_variant != b->variant)) {
     // kernel attributes are set outside the capture
     e = lbm::launch_batched_step(b->nh, b->collapse, b->d_cases, b->d_work, 0, 0, b->stream, b->variant);

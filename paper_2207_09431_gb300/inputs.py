@@ -200,3 +200,46 @@ def ensemble_cases(ncases=128, seed=0, grids=ENSEMBLE_GRIDS, density_ratio=100.0
         cases.append((p, [(nx / 2.0, 0.3 * ny, R, 3)],
                       dict(n=n, Eo=Eo, log10_Mo=log_mo, density_ratio=density_ratio)))
     return cases
+
+
+# ------------------------------------------------------------------ surrogate
+
+MLP_SIZES = (5, 128, 128, 128, 2)
+
+
+def mlp_init(members=1, seed=0):
+    """Initial weights of the surrogate members, flat per member in the layout
+    W_1 (out x in, row-major), b_1, W_2, b_2, ...: W uniform in
+    [-sqrt(6/(in+out)), +sqrt(6/(in+out))] (Glorot and Bengio 2010) from
+    SplitMix64, biases zero.  Returns (members, P) float64."""
+    flat = []
+    for m in range(members):
+        parts = []
+        ctr = 0
+        for l in range(len(MLP_SIZES) - 1):
+            fan_in, fan_out = MLP_SIZES[l], MLP_SIZES[l + 1]
+            a = math.sqrt(6.0 / (fan_in + fan_out))
+            cnt = fan_in * fan_out
+            u = uniform_noise(seed * 1000003 + m, np.arange(ctr, ctr + cnt, dtype=np.uint64), 1.0)
+            ctr += cnt
+            parts.append(a * u)
+            parts.append(np.zeros(fan_out))
+        flat.append(np.concatenate(parts))
+    return np.stack(flat)
+
+
+def mlp_unflatten(w):
+    """Flat member vector -> list of (W, b) in the network's layout."""
+    out, o = [], 0
+    for l in range(len(MLP_SIZES) - 1):
+        i, j = MLP_SIZES[l], MLP_SIZES[l + 1]
+        W = np.asarray(w[o:o + i * j]).reshape(j, i)
+        o += i * j
+        b = np.asarray(w[o:o + j])
+        o += j
+        out.append((W, b))
+    return out
+
+
+def mlp_flatten(params):
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params])

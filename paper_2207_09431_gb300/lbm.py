@@ -69,7 +69,8 @@ EXPORTED = ["lbm_version", "lbm_required_bytes", "lbm_create", "lbm_init_bubbles
             "lbm_profile_step", "lbm_observables_static", "lbm_autotune", "lbm_kernel_config_count",
             "lbm_set_kernel_config", "lbm_batch_required_bytes", "lbm_batch_create", "lbm_batch_case",
             "lbm_batch_set_active", "lbm_batch_step", "lbm_batch_autotune", "lbm_batch_destroy",
-            "lbm_batch_last_error"]
+            "lbm_batch_last_error", "surr_param_count", "surr_required_bytes", "surr_create", "surr_destroy",
+            "surr_last_error", "surr_get_weights", "surr_forward_backward", "surr_train", "surr_predict"]
 
 
 def load_library(path: str | None = None):
@@ -118,6 +119,19 @@ def load_library(path: str | None = None):
     lib.lbm_batch_destroy.restype = None
     lib.lbm_batch_last_error.argtypes = [vp]
     lib.lbm_batch_last_error.restype = ctypes.c_char_p
+    lib.surr_param_count.restype = ctypes.c_int
+    lib.surr_required_bytes.restype = ctypes.c_size_t
+    lib.surr_required_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.surr_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, d, vp, ctypes.c_size_t, vp, P(vp)]
+    lib.surr_destroy.argtypes = [vp]
+    lib.surr_destroy.restype = None
+    lib.surr_last_error.argtypes = [vp]
+    lib.surr_last_error.restype = ctypes.c_char_p
+    lib.surr_get_weights.argtypes = [vp, ctypes.c_int, d]
+    lib.surr_forward_backward.argtypes = [vp, ctypes.c_int, d, d, ctypes.c_int, d, d, d]
+    lib.surr_train.argtypes = [vp, d, d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_ulonglong, d]
+    lib.surr_predict.argtypes = [vp, d, ctypes.c_int, d, d, P(ctypes.c_int)]
     lib.lbm_observables_static.argtypes = [P(lbm_params), vp, vp, ctypes.c_int, ctypes.c_longlong, d, vp]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
@@ -357,7 +371,9 @@ class Batch:
         if self.nbytes == 0:
             raise LbmError(-1, "invalid batch parameters")
         self.arena = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
-        self.stream = stream if stream is not None else torch.cuda.current_stream(self.arena.device)
+        # a created stream, so that runs of steps can be captured as CUDA graphs
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.arena.device)
+        torch.cuda.current_stream(self.arena.device).synchronize()
         self.b = lbm_batch_create(prs, self.arena.data_ptr(), self.nbytes, self.stream.cuda_stream)
 
     def __del__(self):
@@ -402,6 +418,110 @@ class CaseView:
 
     def field(self, name) -> np.ndarray:
         return lbm_get_field(self.h, name, self.nx, self.ny, self.nh)
+
+
+def _check_surr(n, rc, what):
+    if rc != 0:
+        msg = load_library().surr_last_error(n).decode() if n else ""
+        raise LbmError(rc, f"{what}: {msg}")
+
+
+def surr_param_count() -> int:
+    return int(load_library().surr_param_count())
+
+
+def surr_required_bytes(members: int, max_batch: int, max_rows: int) -> int:
+    return int(load_library().surr_required_bytes(members, max_batch, max_rows))
+
+
+def surr_create(members, max_batch, max_rows, init_weights, arena_ptr, arena_bytes, stream_ptr):
+    w = np.ascontiguousarray(init_weights, dtype=np.float64)
+    n = ctypes.c_void_p()
+    rc = load_library().surr_create(int(members), int(max_batch), int(max_rows), _dptr(w), ctypes.c_void_p(arena_ptr),
+                                    arena_bytes, ctypes.c_void_p(stream_ptr), ctypes.byref(n))
+    _check_surr(None, rc, "surr_create")
+    return n
+
+
+def surr_destroy(n):
+    if n:
+        load_library().surr_destroy(n)
+
+
+def surr_get_weights(n, member: int) -> np.ndarray:
+    out = np.zeros(surr_param_count())
+    _check_surr(n, load_library().surr_get_weights(n, int(member), _dptr(out)), "surr_get_weights")
+    return out
+
+
+def surr_forward_backward(n, member, X, T=None):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    rows = X.shape[0]
+    Y = np.zeros((rows, 2))
+    loss = np.zeros(1)
+    grads = np.zeros(surr_param_count())
+    Tp = None
+    if T is not None:
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        Tp = _dptr(T)
+    rc = load_library().surr_forward_backward(n, int(member), _dptr(X), Tp, rows, _dptr(Y), _dptr(loss), _dptr(grads))
+    _check_surr(n, rc, "surr_forward_backward")
+    return Y, float(loss[0]), grads
+
+
+def surr_train(n, X, Y, epochs, batch, lr, seed=0) -> float:
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    fl = np.zeros(1)
+    rc = load_library().surr_train(n, _dptr(X), _dptr(Y), X.shape[0], int(epochs), int(batch), float(lr), int(seed),
+                                   _dptr(fl))
+    _check_surr(n, rc, "surr_train")
+    return float(fl[0])
+
+
+def surr_predict(n, X):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    rows = X.shape[0]
+    mean, spread = np.zeros((rows, 2)), np.zeros((rows, 2))
+    outside = (ctypes.c_int * rows)()
+    rc = load_library().surr_predict(n, _dptr(X), rows, _dptr(mean), _dptr(spread), outside)
+    _check_surr(n, rc, "surr_predict")
+    return mean, spread, np.array(list(outside), dtype=bool)
+
+
+class Surrogate:
+    """Ensemble network with its torch-allocated arena and stream."""
+
+    def __init__(self, init_weights, max_batch=1024, max_rows=4096, device="cuda", stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU path exists)")
+        w = np.atleast_2d(np.asarray(init_weights, dtype=np.float64))
+        self.members = w.shape[0]
+        self.nbytes = surr_required_bytes(self.members, max_batch, max_rows)
+        self.arena = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.arena.device)
+        self.n = surr_create(self.members, max_batch, max_rows, w, self.arena.data_ptr(), self.nbytes,
+                             self.stream.cuda_stream)
+
+    def __del__(self):
+        n = getattr(self, "n", None)
+        if n:
+            surr_destroy(n)
+            self.n = None
+
+    def forward_backward(self, member, X, T=None):
+        return surr_forward_backward(self.n, member, X, T)
+
+    def weights(self, member=0):
+        return surr_get_weights(self.n, member)
+
+    def train(self, X, Y, epochs, batch, lr, seed=0):
+        return surr_train(self.n, X, Y, epochs, batch, lr, seed)
+
+    def predict(self, X):
+        return surr_predict(self.n, X)
 
 
 class Lattice:

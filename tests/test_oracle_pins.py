@@ -300,3 +300,51 @@ def test_oracle_bubble_init_matches_input_generator():
     # disc profile of Eq. 42 at the centre and one radius out
     assert abs(C[0][32, 32] - (0.5 + 0.5 * math.tanh(-10 / 2.0))) < 2e-8
     assert abs(C[0][32, 42] - 0.5) < 2e-8
+
+
+# ------------------------------------------------------------- surrogate MLP
+def test_mlp_oracle_gradients_finite_differences():
+    """Backward pass of the FP64 network against central finite differences."""
+    from oracle import mlp
+
+    w = inputs.mlp_init(1, seed=3)[0]
+    params = inputs.mlp_unflatten(w)
+    rng = np.random.default_rng(0)
+    X, T = rng.normal(size=(6, 5)), rng.normal(size=(6, 2))
+    Y, cache = mlp.forward(params, X, bf16=False)
+    grads = mlp.backward(params, cache, Y, T, bf16=False)
+    flat_g = inputs.mlp_flatten(grads)
+    idx = rng.choice(w.size, size=40, replace=False)
+    for i in idx:
+        h = 1e-6
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        lp = mlp.loss(mlp.forward(inputs.mlp_unflatten(wp), X, bf16=False)[0], T)
+        lm = mlp.loss(mlp.forward(inputs.mlp_unflatten(wm), X, bf16=False)[0], T)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - flat_g[i]) <= 1e-7 + 1e-5 * abs(fd)
+
+
+def test_mlp_oracle_adam_first_step_closed_form():
+    """First Adam step: bias-corrected moments are g and g^2, so the update is
+    -lr g / (|g| + eps) (Kingma and Ba 2015, Algorithm 1)."""
+    from oracle import mlp
+
+    params = inputs.mlp_unflatten(inputs.mlp_init(1, seed=4)[0])
+    rng = np.random.default_rng(1)
+    grads = [(rng.normal(size=W.shape), rng.normal(size=b.shape)) for W, b in params]
+    lr, eps = 1e-3, 1e-8
+    new, _ = mlp.adam(params, grads, mlp.adam_state(params), lr, eps=eps)
+    for (W, b), (W2, b2), (gW, gb) in zip(params, new, grads):
+        assert np.allclose(W2 - W, -lr * gW / (np.abs(gW) + eps), rtol=1e-12, atol=1e-15)
+        assert np.allclose(b2 - b, -lr * gb / (np.abs(gb) + eps), rtol=1e-12, atol=1e-15)
+
+
+def test_bf16_rounding_reference_values():
+    """Round to nearest even at 8 mantissa bits (bfloat16)."""
+    from oracle import mlp
+
+    vals = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -9, np.float32(np.pi), -2.5, 1.0 + 2.0 ** -7 + 2.0 ** -8])
+    want = np.array([1.0, 1.0, 1.0 + 2.0 ** -7, 3.140625, -2.5, 1.0 + 2.0 ** -6])
+    assert np.array_equal(mlp.round_bf16(vals), want)
