@@ -169,15 +169,36 @@ def three_comp_case(nx=256, mobility=0, seed=0, max_draws=100000):
     return p, centres
 
 
+def layered_channel_case(n, k, force, tau_outer=0.8, H=25, nx=2, xi=4.0, sigma=5e-4, tau_min=0.02, tau_max=20.0):
+    """Two-phase layered channel of Sec. 3.3: walls at y = -0.5 and y = 2H - 0.5
+    (half-way bounce-back), periodic in x, a uniform body force along x, equal
+    densities, and the fluid at |y - H + 0.5| < H/2 different from the fluid
+    outside.  The paper puts the power-law fluid (its component 3) in the
+    middle and a Newtonian one outside; here the power-law fluid is component 1
+    (the component whose relaxation time the power law sets) and the outer
+    Newtonian fluid component 3 with tau_outer, the same flow with the labels
+    swapped.  Returns (params, C) with the tanh profile of Eq. 42 across the
+    two flat interfaces."""
+    ny = 2 * H
+    y = np.arange(ny) + 0.5 - H
+    C1 = 0.5 - 0.5 * np.tanh((np.abs(y) - 0.5 * H) / (0.5 * xi))
+    p = dict(nx=nx, ny=ny, ncomp=2, rho=(1.0, 1.0, 1.0), tau=(tau_outer, tau_outer, tau_outer), powerlaw=1,
+             pl_n=n, pl_k=k, tau_min=tau_min, tau_max=tau_max, force_x=force, sigma12=sigma, sigma13=sigma,
+             sigma23=sigma, xi=xi, D0=xi / 300.0)
+    return p, np.repeat(C1[None, :, None], nx, axis=2)
+
+
 ENSEMBLE_GRIDS = ((100, 200), (150, 300), (200, 400), (300, 600))
 
 
-def ensemble_cases(ncases=128, seed=0, grids=ENSEMBLE_GRIDS, density_ratio=100.0):
+def ensemble_cases(ncases=128, seed=0, grids=ENSEMBLE_GRIDS, density_ratio=100.0, mobility=0):
     """Seeded rising-bubble cases: grid drawn from ``grids``, R = nx / 8,
     n ~ U[0.4, 1.0], Eo ~ U[1, 100], log10 Mo ~ U[-3, 1] (Mo taken with the
     velocity scale sqrt(g d)), g from sqrt(g d) = 0.01.  Density ratio 100 by
     default: at 1000 the printed scheme diverges within 100 steps for the
-    R = 12.5 bubbles of the smallest grid (measured with the oracle)."""
+    R = 12.5 bubbles of the smallest grid (measured with the oracle).  Constant
+    mobility by default: with the variable mobility as printed, C undershoots
+    grow and the 100 x 200 cases diverge within 2000 steps (oracle)."""
     cases = []
     for c in range(ncases):
         z = splitmix64_at(seed + 7919 * c, np.arange(4, dtype=np.uint64))
@@ -196,7 +217,7 @@ def ensemble_cases(ncases=128, seed=0, grids=ENSEMBLE_GRIDS, density_ratio=100.0
         # Mo = g drho / (rho_l^2 sigma^3) [k (U/d)^(n-1)]^4  ->  k
         k = (10.0 ** log_mo * sigma ** 3 / (g * drho)) ** 0.25 / (U / d) ** (n - 1.0)
         p = rising_bubble_params(nx, ny, density_ratio=density_ratio, n=n, k=k, sigma=sigma,
-                                 gravity=g, mobility=1)
+                                 gravity=g, mobility=mobility)
         cases.append((p, [(nx / 2.0, 0.3 * ny, R, 3)],
                       dict(n=n, Eo=Eo, log10_Mo=log_mo, density_ratio=density_ratio)))
     return cases
