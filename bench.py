@@ -117,6 +117,35 @@ def gpu_id_for_smi(local, torch):
         return vis.split(",")[local] if vis else str(local)
 
 
+KERNEL_SOURCES = ("paper_2207_09431_gb300/csrc/lbm_fused.cu", "paper_2207_09431_gb300/csrc/lbm_device.cuh",
+                  "paper_2207_09431_gb300/csrc/lbm_devparams.h", "paper_2207_09431_gb300/csrc/lbm_kernels.h")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, nodes: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json: bytes per node measured on a smaller case), or None
+    when the kernel sources changed since that capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    per_node = d.get("bytes_per_node", {}).get(kernel)
+    return None if per_node is None else round(per_node * nodes)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -202,7 +231,8 @@ def run_ours(args):
         dom = "step"
         achieved = step_bytes_per_node(nh) * nodes / (ms_max / args.steps * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": profiled_traffic(dom, nodes), "traffic_unit": "bytes per launch",
                 "step_bytes_per_node": step_bytes_per_node(nh),
                 "step_frac": round(step_bytes_per_node(nh) * nodes / (ms_max / args.steps * 1e-3) / 1e9 / hbm, 4)}
 
@@ -235,6 +265,8 @@ def run_ours(args):
         "kernel_config": kernel_config,
         "observables_after": {"rise_velocity": obs["rise_velocity"], "mass1": obs["mass"][0]},
     }
+    line["collapsed"] = run_state_form(args, torch, dev, stream, C, hbm, storage=0)
+    line["fp16_storage"] = run_state_form(args, torch, dev, stream, C, hbm, storage=1)
     if not args.no_batched:
         line["batched"] = run_batched(args, torch, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -243,6 +275,33 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_state_form(args, torch, dev, stream, C, hbm, storage):
+    """The same workload with the state held as C instead of h (collapse_h):
+    88 algorithmic bytes per node-step instead of 152; with storage = 1 g is
+    also kept as FP16 deviations from an FP32 per-node reference: 60 bytes."""
+    from paper_2207_09431_gb300 import lbm
+
+    p, _ = inputs.sweep_case(args.nx)
+    p = dict(p, collapse_h=1, storage=storage)
+    nodes = p["nx"] * p["ny"]
+    lat = lbm.Lattice(p, device=dev, stream=stream)
+    lat.set_fields(C)
+    name = lat.autotune(reps=5)
+    lat.step(max(3, args.warmup))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    lat.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    bpn = 2 * (9 * 2 + 4 + 4 + 4) if storage else 4 * 2 * (9 + 1 + 1)
+    gbs = bpn * nodes / (ms * 1e-3) / 1e9
+    state = "FP16 g deviations + FP32 reference, C, tau" if storage else "g, C, tau (collapse_h = 1)"
+    return {"state": state, "mlups": round(nodes / (ms * 1e3), 1), "ms_per_step": round(ms, 4),
+            "bytes_per_node": bpn, "achieved_gbs": round(gbs, 1), "frac": round(gbs / hbm, 4), "kernel": name}
 
 
 STEPS_TO_TERMINAL = 50000  # time steps a rising-bubble case needs to reach its terminal velocity

@@ -64,7 +64,13 @@ typedef struct {
   double gravity;      /* g of the body force F_b = -rho g j (Eq. 12) */
   double force_x;      /* uniform body-force density along x (channel flows, Sec. 3.2-3.3) */
   int fd_scheme;       /* directional derivatives: 0 central, 1 mixed central/biased */
-  int storage;         /* population storage: 0 FP32 (only FP32 is accepted) */
+  int storage;         /* state storage: 0 FP32; 1 FP16 g (needs collapse_h = 1): g_a is
+                          kept as the half-precision deviation (g_a - w_a P) s from a
+                          per-node FP32 reference P = sum_a g_a, with a power-of-two
+                          scale s = 2^(14 - ceil(log2 max rho)); C and tau stay FP32
+                          (60 bytes per node-step, 2 components).  Every operation
+                          computes in FP32; only the stored g is rounded.  Batches
+                          need storage 0. */
   int gas_comp;        /* component whose moments lbm_observables reports (2 or 3) */
   int collapse_h;      /* 0: the state holds the populations h^i (Eq. 17-20);
                           1: it holds C_i = sum_a h_a^i instead.  With tau_h = 1/2 the
@@ -197,7 +203,7 @@ lbm_status lbm_postprocess(const lbm_params *p, const double raw[15], lbm_obs *o
  * (a work list of (case, tile) items), and runs of 16 steps are replayed from a
  * captured CUDA graph (on a created stream; on the legacy or per-thread default
  * stream the steps are launched directly).  All cases share ncomp and collapse_h and use
- * fd_scheme 0.  Each case is an ordinary handle carved from the batch arena:
+ * fd_scheme 0 and storage 0.  Each case is an ordinary handle carved from the batch arena:
  * set its initial state, read its observables, fields and checkpoints with the
  * single-lattice calls on lbm_batch_case(b, i); lbm_step on a case advances that
  * case alone.  The arena (>= lbm_batch_required_bytes) and the stream stay the

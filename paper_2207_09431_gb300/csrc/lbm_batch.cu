@@ -102,7 +102,7 @@ size_t lbm_batch_required_bytes(const lbm_params *cases, int ncases) {
   size_t total = 0;
   for (int i = 0; i < ncases; ++i) {
     const size_t b = lbm_required_bytes(&cases[i]);
-    if (b == 0) return 0;
+    if (b == 0 || cases[i].storage != 0) return 0;  // batches hold FP32 states
     total += align_up(b, kAlign);
   }
   total += batch_table_bytes(ncases) + batch_err_bytes(ncases);
@@ -119,8 +119,9 @@ lbm_status lbm_batch_create(const lbm_params *cases, int ncases, void *dev_arena
   if (!dev_arena || ((uintptr_t)dev_arena % kAlign) != 0) return LBM_E_INVAL;
   if (arena_bytes < need) return LBM_E_NOMEM;
   for (int i = 0; i < ncases; ++i) {
-    if (cases[i].ncomp != cases[0].ncomp || cases[i].collapse_h != cases[0].collapse_h || cases[i].fd_scheme != 0)
-      return LBM_E_INVAL;  // one kernel: same component count and state form, central differences
+    if (cases[i].ncomp != cases[0].ncomp || cases[i].collapse_h != cases[0].collapse_h || cases[i].fd_scheme != 0 ||
+        cases[i].storage != 0)
+      return LBM_E_INVAL;  // one kernel: same component count and state form, central differences, FP32
   }
   lbm_batch *b = new (std::nothrow) lbm_batch();
   if (!b) return LBM_E_NOMEM;

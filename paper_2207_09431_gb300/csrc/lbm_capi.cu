@@ -122,6 +122,7 @@ lbm_status lbm_set_fields(lbm_handle *h, const double *C, const double *p, const
   if (e != cudaSuccess) return h->cuda_fail(e, "lbm_set_fields upload");
   // equilibria into buffer 0
   lbm::StepBuffers B = h->buffers(1);  // *_out of buffer index 1 is buffer 0
+  if (h->dp.g16) B.g_out = h->g[1];    // FP32 equilibria into the spare, encoded below
   if (h->prm.collapse_h) {
     B.C = h->C;
     B.h_out = nullptr;
@@ -130,6 +131,7 @@ lbm_status lbm_set_fields(lbm_handle *h, const double *C, const double *p, const
   }
   lbm::launch_init(h->dp, B, h->stream);
   e = cudaGetLastError();
+  if (e == cudaSuccess && h->dp.g16) e = lbm::launch_g16_encode(h->dp, h->g[1], h->g[0], h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "lbm_set_fields init kernel");
   h->cur = 0;
@@ -195,9 +197,21 @@ lbm_status lbm_step(lbm_handle *h, long long nsteps) {
   return LBM_OK;
 }
 
+// FP32 populations of the current state: the state itself, or (FP16 storage)
+// their decoded copy in the spare buffer.
+static const float *fp32_populations(lbm_handle *h, cudaError_t *e) {
+  if (!h->dp.g16) return h->g[h->cur];
+  *e = lbm::launch_g16_decode(h->dp, h->g[h->cur], h->g[1 - h->cur], h->stream);
+  return h->g[1 - h->cur];
+}
+
 static lbm_status compute_macros(lbm_handle *h) {
-  lbm::launch_macros(h->dp, h->buffers(h->cur), h->stream);
-  cudaError_t e = cudaGetLastError();
+  lbm::StepBuffers B = h->buffers(h->cur);
+  cudaError_t e = cudaSuccess;
+  B.g_in = fp32_populations(h, &e);
+  if (e != cudaSuccess) return h->cuda_fail(e, "FP16 decode");
+  lbm::launch_macros(h->dp, B, h->stream);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return h->cuda_fail(e, "macro kernels");
   return LBM_OK;
 }
@@ -299,7 +313,11 @@ lbm_status lbm_get_field(lbm_handle *h, int id, double *out, size_t n) {
   const size_t pf = h->L.plane_bytes / sizeof(float);
   cudaError_t e = cudaSuccess;
   switch (id) {
-    case LBM_FIELD_G: e = download_planes(h, h->g[h->cur], out, 9); break;
+    case LBM_FIELD_G: {
+      const float *g32 = fp32_populations(h, &e);
+      if (e == cudaSuccess) e = download_planes(h, g32, out, 9);
+      break;
+    }
     case LBM_FIELD_H:
       if (h->prm.collapse_h) return h->fail(LBM_E_STATE, "the collapsed state form stores no h populations");
       e = download_planes(h, h->h[h->cur], out, 9 * nh);

@@ -7,6 +7,8 @@ namespace lbm {
 struct DevParams {
   int nx, ny, pitch, ncomp, nh, periodic_y, powerlaw, mobility, fd_scheme;
   int collapse_h;  // 1: the state holds C_i instead of the populations h^i
+  int g16;         // 1: g stored as FP16 deviations (with collapse_h)
+  float g16_scale, g16_inv_scale;
   float rho[3], tau[3];
   float pl_n, pl_k, tau_min, tau_max;
   float sig12, sig13, sig23, Lambda, Sig[3], SigT, xi, D0;

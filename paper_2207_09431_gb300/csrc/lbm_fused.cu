@@ -19,6 +19,8 @@
 // halo rings are re-read through L2.  Ghost rows beyond a wall hold mirrored
 // values (R10): loaded data is mirrored pointwise, stencil-derived mu and p are
 // copied from the mirror slot.
+#include <cuda_fp16.h>
+
 #include "lbm_device.cuh"
 #include "lbm_kernels.h"
 
@@ -72,16 +74,36 @@ __device__ __forceinline__ int i2(int lx, int ly) { return (ly + 2) * (TX + 4) +
 template <int TX>
 __device__ __forceinline__ int i1(int lx, int ly) { return (ly + 1) * (TX + 2) + (lx + 1); }
 
+// FP16 deviation codec of the FORM 2 state (below).  One rounding order for
+// every encoder and decoder, so that a decode-encode round trip is exact.
+__device__ __forceinline__ float g16_decode(float Pref, __half d, int a, float inv_scale) {
+  return __fmaf_rn(wt(a), Pref, __half2float(d) * inv_scale);
+}
+__device__ __forceinline__ __half g16_encode(float g, float Pref, int a, float scale) {
+  return __float2half_rn(__fmaf_rn(-wt(a), Pref, g) * scale);
+}
+__device__ __forceinline__ float g16_reference(const float (&g)[9]) {
+  float Pn = 0.f;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) Pn += g[a];
+  return Pn;
+}
+
 }  // namespace
 
-// STORE_H = true: the state holds the populations h^i (the method's state).
-// STORE_H = false: the state holds C_i only.  With tau_h = 1/2 the collision
-// of Eq. 18 depends on h only through C_i = sum_a h_a^i, so C_i(t+1) =
-// sum_a h_a^i(t+1) carries the same information (same results up to the order
-// of the FP32 sums) at 88 instead of 152 bytes per node-step.
+// FORM 0: the state holds the populations h^i (the method's state).
+// FORM 1: the state holds C_i only.  With tau_h = 1/2 the collision of Eq. 18
+// depends on h only through C_i = sum_a h_a^i, so C_i(t+1) = sum_a h_a^i(t+1)
+// carries the same information (same results up to the order of the FP32
+// sums) at 88 instead of 152 bytes per node-step.
+// FORM 2: as FORM 1, and g is stored as FP16 deviations from a per-node
+// reference: d_a = (g_a - w_a P) * scale with P = sum_a g_a kept in FP32 (the
+// pressure-sized part stays in FP32, only the small deviations go to FP16),
+// 60 bytes per node-step.  In memory: 9 half planes, then the FP32 P plane,
+// inside the space of the 9 FP32 planes.
 // NT threads per CTA (NT >= TX * TY); NT close to the size of R1 lets the
 // heaviest stage run in one pass.
-template <int TX, int TY, int NH, bool STORE_H, int NT>
+template <int TX, int TY, int NH, int FORM, int NT>
 __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffers &B, int x0, int y0,
                                            Smem<TX, TY, NH> &s) {
   using S = Smem<TX, TY, NH>;
@@ -97,7 +119,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
       float acc;
-      if constexpr (STORE_H) {
+      if constexpr (FORM == 0) {
         acc = 0.f;
 #pragma unroll
         for (int a = 0; a < 9; ++a) acc += B.h_in[((long long)i * 9 + a) * plane + k];
@@ -119,9 +141,17 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
     if (!per && (gy < 0 || gy >= ny)) continue;
     const long long k = (long long)(per ? wrap_periodic(gy, ny) : gy) * pitch + wrap_periodic(x0 + lx, nx);
     float m0 = 0.f, mx = 0.f, my = 0.f;
+    float Pref = 0.f;
+    if constexpr (FORM == 2) Pref = B.g_in[(9 * plane) / 2 + k];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const float ga = B.g_in[(long long)a * plane + k];
+      float ga;
+      if constexpr (FORM == 2) {
+        const __half *gh = reinterpret_cast<const __half *>(B.g_in);
+        ga = g16_decode(Pref, gh[(long long)a * plane + k], a, P.g16_inv_scale);
+      } else {
+        ga = B.g_in[(long long)a * plane + k];
+      }
       s.g[a][q] = ga;
       m0 += ga;
       mx += ex(a) * ga;
@@ -206,6 +236,16 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
     const int c3 = i3<TX>(lx, ly);
     const float ux = s.ux[c2], uy = s.uy[c2], p = s.p[c2], rho = s.rho[c3];
     const float irho = 1.0f / rho;
+    // neighbour values, loaded once: p (2-ring), rho and C (3-ring)
+    float pn[9], rn[9], cn[NH][9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const int j2 = c2 + ey(a) * S::W2 + ex(a), j3 = c3 + ey(a) * S::W3 + ex(a);
+      pn[a] = s.p[j2];
+      rn[a] = s.rho[j3];
+#pragma unroll
+      for (int i = 0; i < NH; ++i) cn[i][a] = s.C[i][j3];
+    }
     // gradients of p and mu on R2
     float px = 0.f, py = 0.f, mgx[NH], mgy[NH], mlap[NH];
 #pragma unroll
@@ -213,7 +253,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
       const int j2 = c2 + ey(a) * S::W2 + ex(a);
-      const float pv = s.p[j2];
+      const float pv = pn[a];
       px += wt(a) * ex(a) * pv;
       py += wt(a) * ey(a) * pv;
 #pragma unroll
@@ -260,15 +300,14 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
       const float exa = (float)ex(a), eya = (float)ey(a), w = wt(a);
       const float eu = exa * ux + eya * uy;
       const float G = w * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-      const int jp3 = c3 + ey(a) * S::W3 + ex(a), jm3 = c3 - ey(a) * S::W3 - ex(a);
-      const int jp2 = c2 + ey(a) * S::W2 + ex(a), jm2 = c2 - ey(a) * S::W2 - ex(a);
-      const float dr = 0.5f * (s.rho[jp3] - s.rho[jm3]);
-      const float dp = 0.5f * (s.p[jp2] - s.p[jm2]);
+      // directional derivatives from the neighbour registers (x + e_a, x - e_a)
+      const float dr = 0.5f * (rn[a] - rn[opp(a)]);
+      const float dp = 0.5f * (pn[a] - pn[opp(a)]);
       float dC[NH];
       float eFs = -udFs;
 #pragma unroll
       for (int i = 0; i < NH; ++i) {
-        dC[i] = 0.5f * (s.C[i][jp3] - s.C[i][jm3]);
+        dC[i] = 0.5f * (cn[i][a] - cn[i][opp(a)]);
         eFs += dmu[i] * dC[i];
       }
       const float eFb = exa * P.force_x + eya * Fby - udFb;
@@ -327,6 +366,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
     svy[i] = 0.5f * s.sv[i][yc1];
     csum[i] = 0.f;
   }
+  float gy[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     int s1 = yc1 - ey(a) * S::W1 - ex(a);
@@ -340,37 +380,48 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
         b = opp(a);
       }
     }
-    B.g_out[(long long)a * plane + ky] = s.g[b][s2];
+    if constexpr (FORM == 2) {
+      gy[a] = s.g[b][s2];
+    } else {
+      B.g_out[(long long)a * plane + ky] = s.g[b][s2];
+    }
     const float euy = ex(a) * uxy + ey(a) * uyy;
     const float Gy = wt(a) * (1.0f + 3.0f * euy + 4.5f * euy * euy - 1.5f * uuy);
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
       const float hv = s.hs[i][b][s1] + svy[i] * Gy;
-      if constexpr (STORE_H) {
+      if constexpr (FORM == 0) {
         B.h_out[((long long)i * 9 + a) * plane + ky] = hv;
       } else {
         csum[i] += hv;
       }
     }
   }
-  if constexpr (!STORE_H) {
+  if constexpr (FORM != 0) {
 #pragma unroll
     for (int i = 0; i < NH; ++i) B.h_out[(long long)i * plane + ky] = csum[i];
+  }
+  if constexpr (FORM == 2) {
+    const float Pn = g16_reference(gy);
+    B.g_out[(9 * plane) / 2 + ky] = Pn;
+    __half *gh = reinterpret_cast<__half *>(B.g_out);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) gh[(long long)a * plane + ky] = g16_encode(gy[a], Pn, a, P.g16_scale);
   }
 }
 
 // One lattice: tile (blockIdx.x, blockIdx.y).
-template <int TX, int TY, int NH, bool STORE_H, int NT, int MINB>
+template <int TX, int TY, int NH, int FORM, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_step_fused(DevParams P, FusedBuffers B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fused_tile<TX, TY, NH, STORE_H, NT>(P, B, blockIdx.x * TX, blockIdx.y * TY,
+  fused_tile<TX, TY, NH, FORM, NT>(P, B, blockIdx.x * TX, blockIdx.y * TY,
                                       *reinterpret_cast<Smem<TX, TY, NH> *>(smem_raw));
 }
 
 // Many lattices in one launch: CTA b takes work item b = (case, tile origin);
 // the case's parameters and buffers are staged in shared memory.  parity
 // selects which of the case's two buffer sets is the input this step.
-template <int TX, int TY, int NH, bool STORE_H, int NT, int MINB>
+template <int TX, int TY, int NH, int FORM, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_step_batched(const BatchCase *__restrict__ cases,
                                                            const WorkItem *__restrict__ work, int parity) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -382,129 +433,173 @@ __global__ void __launch_bounds__(NT, MINB) k_step_batched(const BatchCase *__re
     sB = cases[w.case_id].B[cases[w.case_id].base_parity ^ parity];
   }
   __syncthreads();
-  fused_tile<TX, TY, NH, STORE_H, NT>(sP, sB, w.x0, w.y0, *reinterpret_cast<Smem<TX, TY, NH> *>(smem_raw));
+  fused_tile<TX, TY, NH, FORM, NT>(sP, sB, w.x0, w.y0, *reinterpret_cast<Smem<TX, TY, NH> *>(smem_raw));
 }
 
 // ---------------------------------------------------------------- launcher
 
-template <int TX, int TY, int NH, bool STORE_H, int NT, int MINB>
+template <int TX, int TY, int NH, int FORM, int NT, int MINB>
 static cudaError_t launch_fused_t(const DevParams &P, const FusedBuffers &B, cudaStream_t s) {
   static_assert(NT >= TX * TY, "one thread per output node in stage 3");
   const size_t smem = sizeof(Smem<TX, TY, NH>);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_fused<TX, TY, NH, STORE_H, NT, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(k_step_fused<TX, TY, NH, FORM, NT, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const dim3 grd((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  k_step_fused<TX, TY, NH, STORE_H, NT, MINB><<<grd, NT, smem, s>>>(P, B);
+  k_step_fused<TX, TY, NH, FORM, NT, MINB><<<grd, NT, smem, s>>>(P, B);
   return cudaGetLastError();
 }
 
 // nwork == 0 only sets the kernel's shared-memory attribute (done before any
 // stream capture).
-template <int TX, int TY, int NH, bool STORE_H, int NT, int MINB>
+template <int TX, int TY, int NH, int FORM, int NT, int MINB>
 static cudaError_t launch_batched_t(const BatchCase *cases, const WorkItem *work, int nwork, int parity,
                                    cudaStream_t s) {
   const size_t smem = sizeof(Smem<TX, TY, NH>);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_batched<TX, TY, NH, STORE_H, NT, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(k_step_batched<TX, TY, NH, FORM, NT, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   if (nwork <= 0) return cudaSuccess;
-  k_step_batched<TX, TY, NH, STORE_H, NT, MINB><<<nwork, NT, smem, s>>>(cases, work, parity);
+  k_step_batched<TX, TY, NH, FORM, NT, MINB><<<nwork, NT, smem, s>>>(cases, work, parity);
   return cudaGetLastError();
 }
 
 // Launch configurations the autotuner chooses from: output tile TX x TY,
 // threads per CTA (sized to one of the rings so that a heavy stage runs in a
 // single pass) and the minimum resident CTAs per SM passed to the compiler.
-template <int NH, bool STORE_H>
+template <int NH, int FORM>
 struct VariantTable {
-  static constexpr int kCount = NH == 1 ? 4 : 2;
+  static constexpr int kCount = FORM == 2 ? 2 : (NH == 1 ? 5 : 2);
   static const char *name(int v) {
-    static const char *n1[4] = {"32x8/352/3", "32x8/448/2", "32x16/640/2", "64x8/704/1"};
+    static const char *n1[5] = {"32x8/352/3", "32x8/448/2", "32x16/640/2", "64x8/704/1", "32x8/352/2"};
     static const char *n2[2] = {"32x8/352/2", "32x8/448/2"};
-    return NH == 1 ? n1[v] : n2[v];
+    static const char *n16[2] = {"32x8/352/3", "32x8/352/2"};
+    return (FORM == 2 && NH == 1) ? n16[v] : (NH == 1 ? n1[v] : n2[v]);
   }
   static void tile(int v, int *tx, int *ty) {
-    static const int t1[4][2] = {{32, 8}, {32, 8}, {32, 16}, {64, 8}};
-    *tx = t1[NH == 1 ? v : 0][0];
-    *ty = t1[NH == 1 ? v : 0][1];
+    static const int t1[5][2] = {{32, 8}, {32, 8}, {32, 16}, {64, 8}, {32, 8}};
+    *tx = t1[(NH == 1 && FORM != 2) ? v : 0][0];
+    *ty = t1[(NH == 1 && FORM != 2) ? v : 0][1];
   }
   static cudaError_t launch_batched(int v, const BatchCase *c, const WorkItem *w, int n, int parity,
                                     cudaStream_t s) {
-    if constexpr (NH == 1) {
+    if constexpr (FORM == 2) {
+      return cudaErrorNotSupported;  // batches hold FP32 states
+    } else if constexpr (NH == 1) {
       switch (v) {
-        case 1: return launch_batched_t<32, 8, NH, STORE_H, 448, 2>(c, w, n, parity, s);
-        case 2: return launch_batched_t<32, 16, NH, STORE_H, 640, 2>(c, w, n, parity, s);
-        case 3: return launch_batched_t<64, 8, NH, STORE_H, 704, 1>(c, w, n, parity, s);
-        default: return launch_batched_t<32, 8, NH, STORE_H, 352, 3>(c, w, n, parity, s);
+        case 1: return launch_batched_t<32, 8, NH, FORM, 448, 2>(c, w, n, parity, s);
+        case 2: return launch_batched_t<32, 16, NH, FORM, 640, 2>(c, w, n, parity, s);
+        case 3: return launch_batched_t<64, 8, NH, FORM, 704, 1>(c, w, n, parity, s);
+        case 4: return launch_batched_t<32, 8, NH, FORM, 352, 2>(c, w, n, parity, s);
+        default: return launch_batched_t<32, 8, NH, FORM, 352, 3>(c, w, n, parity, s);
       }
     } else {
       switch (v) {
-        case 1: return launch_batched_t<32, 8, NH, STORE_H, 448, 2>(c, w, n, parity, s);
-        default: return launch_batched_t<32, 8, NH, STORE_H, 352, 2>(c, w, n, parity, s);
+        case 1: return launch_batched_t<32, 8, NH, FORM, 448, 2>(c, w, n, parity, s);
+        default: return launch_batched_t<32, 8, NH, FORM, 352, 2>(c, w, n, parity, s);
       }
     }
   }
   static cudaError_t launch(int v, const DevParams &P, const FusedBuffers &B, cudaStream_t s) {
-    if constexpr (NH == 1) {
+    if constexpr (FORM == 2 && NH == 1) {
+      return v == 1 ? launch_fused_t<32, 8, NH, FORM, 352, 2>(P, B, s) : launch_fused_t<32, 8, NH, FORM, 352, 3>(P, B, s);
+    } else if constexpr (NH == 1) {
       switch (v) {
-        case 1: return launch_fused_t<32, 8, NH, STORE_H, 448, 2>(P, B, s);
-        case 2: return launch_fused_t<32, 16, NH, STORE_H, 640, 2>(P, B, s);
-        case 3: return launch_fused_t<64, 8, NH, STORE_H, 704, 1>(P, B, s);
-        default: return launch_fused_t<32, 8, NH, STORE_H, 352, 3>(P, B, s);
+        case 1: return launch_fused_t<32, 8, NH, FORM, 448, 2>(P, B, s);
+        case 2: return launch_fused_t<32, 16, NH, FORM, 640, 2>(P, B, s);
+        case 3: return launch_fused_t<64, 8, NH, FORM, 704, 1>(P, B, s);
+        case 4: return launch_fused_t<32, 8, NH, FORM, 352, 2>(P, B, s);
+        default: return launch_fused_t<32, 8, NH, FORM, 352, 3>(P, B, s);
       }
     } else {
       switch (v) {
-        case 1: return launch_fused_t<32, 8, NH, STORE_H, 448, 2>(P, B, s);
-        default: return launch_fused_t<32, 8, NH, STORE_H, 352, 2>(P, B, s);
+        case 1: return launch_fused_t<32, 8, NH, FORM, 448, 2>(P, B, s);
+        default: return launch_fused_t<32, 8, NH, FORM, 352, 2>(P, B, s);
       }
     }
   }
 };
 
+static int form_of(const DevParams &P) { return P.g16 ? 2 : (P.collapse_h ? 1 : 0); }
+
 int fused_variant_count(const DevParams &P) {
-  return P.nh == 1 ? VariantTable<1, true>::kCount : VariantTable<2, true>::kCount;
+  if (form_of(P) == 2) return P.nh == 1 ? VariantTable<1, 2>::kCount : VariantTable<2, 2>::kCount;
+  return P.nh == 1 ? VariantTable<1, 0>::kCount : VariantTable<2, 0>::kCount;
 }
 
 const char *fused_variant_name(const DevParams &P, int v) {
   if (v < 0 || v >= fused_variant_count(P)) v = 0;
-  return P.nh == 1 ? VariantTable<1, true>::name(v) : VariantTable<2, true>::name(v);
+  if (form_of(P) == 2) return P.nh == 1 ? VariantTable<1, 2>::name(v) : VariantTable<2, 2>::name(v);
+  return P.nh == 1 ? VariantTable<1, 0>::name(v) : VariantTable<2, 0>::name(v);
 }
 
 cudaError_t launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v) {
   if (v < 0 || v >= fused_variant_count(P)) v = 0;
-  if (P.collapse_h) {
-    if (P.nh == 1) return VariantTable<1, false>::launch(v, P, B, s);
-    return VariantTable<2, false>::launch(v, P, B, s);
+  switch (form_of(P)) {
+    case 2: return P.nh == 1 ? VariantTable<1, 2>::launch(v, P, B, s) : VariantTable<2, 2>::launch(v, P, B, s);
+    case 1: return P.nh == 1 ? VariantTable<1, 1>::launch(v, P, B, s) : VariantTable<2, 1>::launch(v, P, B, s);
+    default: return P.nh == 1 ? VariantTable<1, 0>::launch(v, P, B, s) : VariantTable<2, 0>::launch(v, P, B, s);
   }
-  if (P.nh == 1) return VariantTable<1, true>::launch(v, P, B, s);
-  return VariantTable<2, true>::launch(v, P, B, s);
 }
 
 void fused_variant_tile(const DevParams &P, int v, int *tx, int *ty) {
   if (v < 0 || v >= fused_variant_count(P)) v = 0;
-  if (P.nh == 1) VariantTable<1, true>::tile(v, tx, ty);
-  else VariantTable<2, true>::tile(v, tx, ty);
+  if (P.nh == 1) VariantTable<1, 0>::tile(v, tx, ty);
+  else VariantTable<2, 0>::tile(v, tx, ty);
 }
 
 cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
                                 int parity, cudaStream_t s, int v) {
-  const int count = nh == 1 ? VariantTable<1, true>::kCount : VariantTable<2, true>::kCount;
+  const int count = nh == 1 ? VariantTable<1, 0>::kCount : VariantTable<2, 0>::kCount;
   if (v < 0 || v >= count) v = 0;
   if (collapse_h) {
-    if (nh == 1) return VariantTable<1, false>::launch_batched(v, cases, work, nwork, parity, s);
-    return VariantTable<2, false>::launch_batched(v, cases, work, nwork, parity, s);
+    if (nh == 1) return VariantTable<1, 1>::launch_batched(v, cases, work, nwork, parity, s);
+    return VariantTable<2, 1>::launch_batched(v, cases, work, nwork, parity, s);
   }
-  if (nh == 1) return VariantTable<1, true>::launch_batched(v, cases, work, nwork, parity, s);
-  return VariantTable<2, true>::launch_batched(v, cases, work, nwork, parity, s);
+  if (nh == 1) return VariantTable<1, 0>::launch_batched(v, cases, work, nwork, parity, s);
+  return VariantTable<2, 0>::launch_batched(v, cases, work, nwork, parity, s);
+}
+
+// Conversions between the FP32 populations and the FORM 2 storage (initial
+// state, field readback), one thread per node.
+__global__ void k_g16_encode(DevParams P, const float *__restrict__ g32, float *__restrict__ g16) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P.plane) return;
+  float g[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) g[a] = g32[a * P.plane + k];
+  const float Pn = g16_reference(g);
+  g16[(9 * P.plane) / 2 + k] = Pn;
+  __half *gh = reinterpret_cast<__half *>(g16);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) gh[a * P.plane + k] = g16_encode(g[a], Pn, a, P.g16_scale);
+}
+
+__global__ void k_g16_decode(DevParams P, const float *__restrict__ g16, float *__restrict__ g32) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P.plane) return;
+  const float Pref = g16[(9 * P.plane) / 2 + k];
+  const __half *gh = reinterpret_cast<const __half *>(g16);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) g32[a * P.plane + k] = g16_decode(Pref, gh[a * P.plane + k], a, P.g16_inv_scale);
+}
+
+cudaError_t launch_g16_encode(const DevParams &P, const float *g32, float *g16, cudaStream_t s) {
+  k_g16_encode<<<(unsigned)((P.plane + 255) / 256), 256, 0, s>>>(P, g32, g16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g16_decode(const DevParams &P, const float *g16, float *g32, cudaStream_t s) {
+  k_g16_decode<<<(unsigned)((P.plane + 255) / 256), 256, 0, s>>>(P, g16, g32);
+  return cudaGetLastError();
 }
 
 bool fused_supported(const DevParams &P) { return P.fd_scheme == 0; }

@@ -61,7 +61,8 @@ inline const char *validate(const lbm_params *p) {
   if ((long long)p->nx * p->ny > (1LL << 31)) return "lattice too large";
   if (p->ncomp != 2 && p->ncomp != 3) return "ncomp must be 2 or 3";
   if (p->fd_scheme != 0 && p->fd_scheme != 1) return "fd_scheme must be 0 or 1";
-  if (p->storage != 0) return "only FP32 storage (0) is supported";
+  if (p->storage != 0 && p->storage != 1) return "storage must be 0 (FP32) or 1 (FP16 g)";
+  if (p->storage == 1 && !p->collapse_h) return "FP16 storage needs collapse_h 1";
   if (p->mobility != 0 && p->mobility != 1) return "mobility must be 0 or 1";
   if (p->gas_comp != 2 && p->gas_comp != 3) return "gas_comp must be 2 or 3";
   if (p->ncomp == 2 && p->gas_comp != 3) return "with two components the gas is component 3";
@@ -92,6 +93,16 @@ inline lbm::DevParams dev_params(const lbm_params &p) {
   d.mobility = p.mobility;
   d.fd_scheme = p.fd_scheme;
   d.collapse_h = p.collapse_h;
+  d.g16 = p.storage == 1 ? 1 : 0;
+  {
+    // power-of-two scale: deviations of size rho_max stay far below the FP16
+    // maximum (65504 / 2^14 = 4 rho_max) while those of size 1e-8 rho_max are
+    // still normal numbers (smallest normal 6.1e-5 / 2^14 = 3.7e-9 rho_max)
+    const double rmax = std::fmax(p.rho[0], std::fmax(p.rho[1], p.rho[2]));
+    const int e = 14 - (int)std::ceil(std::log2(rmax));
+    d.g16_scale = (float)std::ldexp(1.0, e);
+    d.g16_inv_scale = (float)std::ldexp(1.0, -e);
+  }
   for (int i = 0; i < 3; ++i) {
     d.rho[i] = (float)p.rho[i];
     d.tau[i] = (float)p.tau[i];

@@ -49,6 +49,10 @@ cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases,
 int fused_variant_count(const DevParams &P);
 const char *fused_variant_name(const DevParams &P, int v);
 cudaError_t launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v);
+// FP16 storage (P.g16): g32 holds 9 FP32 planes, g16 the same space as 9 half
+// planes followed by the FP32 plane of the per-node reference sum_a g_a.
+cudaError_t launch_g16_encode(const DevParams &P, const float *g32, float *g16, cudaStream_t s);
+cudaError_t launch_g16_decode(const DevParams &P, const float *g16, float *g32, cudaStream_t s);
 
 void launch_macros(const DevParams &P, const StepBuffers &B, cudaStream_t s);
 void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s);

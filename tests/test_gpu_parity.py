@@ -17,6 +17,7 @@ the same case with the FP32 build.
 import numpy as np
 import pytest
 
+import channel_closed_form as ccf
 import oracle
 from paper_2207_09431_gb300 import inputs
 
@@ -263,3 +264,38 @@ def test_full_size_windows(lbm):
             ref = o64.field(n)[sl]
             floor = relerr(o32.field(n)[sl], ref)
             assert relerr(got, ref) <= max(TOL, FLOOR_FACTOR * floor), (n, x0, y0)
+
+
+@pytest.mark.parametrize("n,tau_in", [(0.5, 0.8), (1.0, 0.24)])
+def test_layered_channel_parity(lbm, n, tau_in):
+    """Two-phase layered channel of Sec. 3.3 on a 2 x 50 lattice (narrower than
+    one tile: every x-neighbour wraps), x-forcing, power law in the inner
+    fluid: fields and populations after 2000 steps."""
+    F, k, _ = ccf.design(n, tau_in, 0.8, 25, umax=0.005)
+    p, C = inputs.layered_channel_case(n, k, F, tau_outer=0.8, H=25)
+    c = Case(lbm, p, inputs.round_to_fp32(C))
+    c.step(2000)
+    c.check()
+
+
+def test_layered_channel_steady_state(lbm):
+    """The CUDA path run to the steady state of the layered channel (inner
+    index 1.5, equal interface viscosities) meets the closed form within the
+    error Table 3 prints for that index, and the stress balance to 2e-3."""
+    n, H = 1.5, 25
+    F, k, k_out = ccf.design(n, 0.8, 0.8, H, umax=0.005)
+    p, C = inputs.layered_channel_case(n, k, F, tau_outer=0.8, H=H)
+    lat = lbm.Lattice(p)
+    lat.set_fields(inputs.round_to_fp32(C))
+    prev = None
+    for _ in range(200):
+        lat.step(500)
+        u = lat.field("ux")[:, 0]
+        if prev is not None and np.linalg.norm(u - prev) / np.linalg.norm(u) < 1e-7:
+            break
+        prev = u
+    y = np.arange(2 * H) + 0.5 - H
+    ua = ccf.layered_profile(y, H, 0.5 * H, F, n, k, 1.0, k_out)
+    assert np.linalg.norm(u - ua) / np.linalg.norm(ua) <= 0.01
+    uq = ccf.stress_balance_profile(y, lat.field("tau")[:, 0] / 3.0, F, H)
+    assert np.linalg.norm(u - uq) / np.linalg.norm(uq) <= 2e-3
