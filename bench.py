@@ -45,6 +45,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-cases", type=int, default=128)
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the collapsed and FP16 state-form lines")
+    ap.add_argument("--kernel-config", type=int, default=-1,
+                    help="launch configuration of the step kernel (default: autotuned)")
+    ap.add_argument("--stability", action="store_true",
+                    help="also compare the central and mixed difference schemes on the 36-case paper grid")
     return ap.parse_args()
 
 
@@ -117,7 +123,8 @@ def gpu_id_for_smi(local, torch):
         return vis.split(",")[local] if vis else str(local)
 
 
-KERNEL_SOURCES = ("paper_2207_09431_gb300/csrc/lbm_fused.cu", "paper_2207_09431_gb300/csrc/lbm_device.cuh",
+KERNEL_SOURCES = ("paper_2207_09431_gb300/csrc/lbm_fused.cu", "paper_2207_09431_gb300/csrc/lbm_sweep.cu",
+                  "paper_2207_09431_gb300/csrc/lbm_node.cuh", "paper_2207_09431_gb300/csrc/lbm_device.cuh",
                   "paper_2207_09431_gb300/csrc/lbm_devparams.h", "paper_2207_09431_gb300/csrc/lbm_kernels.h")
 
 
@@ -193,7 +200,11 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     lat = lbm.Lattice(p, device=dev, stream=stream)
     lat.set_fields(C)
-    kernel_config = lat.autotune(reps=5)
+    if args.kernel_config >= 0:
+        lbm.lbm_set_kernel_config(lat.h, args.kernel_config)
+        kernel_config = lbm.lbm_kernel_name(lat.h, 0)
+    else:
+        kernel_config = lat.autotune(reps=5)
     lat.step(args.warmup)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -265,16 +276,36 @@ def run_ours(args):
         "kernel_config": kernel_config,
         "observables_after": {"rise_velocity": obs["rise_velocity"], "mass1": obs["mass"][0]},
     }
-    line["collapsed"] = run_state_form(args, torch, dev, stream, C, hbm, storage=0)
-    line["fp16_storage"] = run_state_form(args, torch, dev, stream, C, hbm, storage=1)
+    if not args.no_forms:
+        line["collapsed"] = run_state_form(args, torch, dev, stream, C, hbm, storage=0)
+        line["fp16_storage"] = run_state_form(args, torch, dev, stream, C, hbm, storage=1)
     if not args.no_batched:
         line["batched"] = run_batched(args, torch, dev, stream)
+    if not args.no_surrogate and rank == 0:
+        line["surrogate"] = run_surrogate(stream)
+    if args.stability and rank == 0:
+        from paper_2207_09431_gb300 import stability
+
+        rows, summary = stability.compare(steps=20000, stream=stream)
+        line["stability"] = {"steps": 20000, "summary": summary, "cases": rows}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(target_s=15.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_surrogate(stream):
+    """C_D error of the surrogate: 1024 seeded 100 x 200 cases solved to their
+    terminal state by the batched solver train the ensemble; 128 held-out cases
+    solved in full judge it (not part of the timed step)."""
+    from paper_2207_09431_gb300 import surrogate
+
+    t0 = time.perf_counter()
+    s = surrogate.evaluate(n_train=1024, n_test=128, stream=stream)
+    s["wall_s"] = round(time.perf_counter() - t0, 1)
+    return s
 
 
 def run_state_form(args, torch, dev, stream, C, hbm, storage):

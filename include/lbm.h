@@ -259,8 +259,9 @@ lbm_status surr_forward_backward(surr_net *n, int member, const double *X, const
  * training hull.  final_loss (may be NULL): loss of the last mini-batch. */
 lbm_status surr_train(surr_net *n, const double *X, const double *Y, int rows, int epochs, int batch, double lr,
                       unsigned long long seed, double *final_loss);
-/* Ensemble mean and spread (max - min) of the two outputs for rows x 5 raw
- * inputs; outside[r] = 1 when input r lies outside the training box. */
+/* Ensemble mean and disagreement (the largest deviation of one member from
+ * the mean) of the two outputs for rows x 5 raw inputs; outside[r] = 1 when
+ * input r lies outside the training box.  y_spread and outside may be NULL. */
 lbm_status surr_predict(surr_net *n, const double *X, int rows, double *y_mean, double *y_spread, int *outside);
 
 /* Largest lattice (nx * ny nodes) lbm_observables_static accepts. */

@@ -66,7 +66,7 @@ struct lbm_batch {
     for (int i = 0; i < n; ++i) {
       if (!active[i] || !h[i]->initialized) continue;
       int tx = 32, ty = 8;
-      lbm::fused_variant_tile(h[i]->dp, v, &tx, &ty);
+      lbm::batched_variant_tile(nh, v, &tx, &ty);
       for (int y0 = 0; y0 < h[i]->dp.ny; y0 += ty)
         for (int x0 = 0; x0 < h[i]->dp.nx; x0 += tx) w.push_back({i, x0, y0});
     }
@@ -166,7 +166,7 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int reps, int *chosen) {
   if (!b || reps < 1) return LBM_E_INVAL;
   cudaError_t e = b->upload_table();
   if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_autotune table");
-  const int nv = lbm::fused_variant_count(b->h[0]->dp);
+  const int nv = lbm::batched_variant_count(b->nh);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return b->fail(LBM_E_CUDA, "cudaEventCreate");

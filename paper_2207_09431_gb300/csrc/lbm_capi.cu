@@ -429,7 +429,8 @@ const char *lbm_kernel_name(const lbm_handle *h, int i) {
   if (!h || i < 0 || i >= h->kernels_per_step()) return "";
   if (!h->fused()) return names[i];
   lbm_handle *m = const_cast<lbm_handle *>(h);
-  m->kname = std::string("k_step_fused[") + lbm::fused_variant_name(h->dp, h->variant) + "]";
+  const bool sweep = h->variant < lbm::sweep_variant_count(h->dp);
+  m->kname = std::string(sweep ? "k_step_sweep[" : "k_step_fused[") + lbm::fused_variant_name(h->dp, h->variant) + "]";
   return m->kname.c_str();
 }
 

@@ -21,30 +21,12 @@
 // copied from the mirror slot.
 #include <cuda_fp16.h>
 
-#include "lbm_device.cuh"
 #include "lbm_kernels.h"
+#include "lbm_node.cuh"
 
 namespace lbm {
 
 namespace {
-
-// Periodic index for offsets of at most one period (the common case) with a
-// modulo fallback for lattices smaller than a tile.
-__device__ __forceinline__ int wrap_periodic(int v, int n) {
-  if (v < 0) v += n;
-  if (v >= n) v -= n;
-  if (v < 0 || v >= n) v = ((v % n) + n) % n;
-  return v;
-}
-
-// Row read for row gy: periodic, or mirrored about the half-way walls; rows far
-// outside (only in unused slots of a ragged tile) are clamped.
-__device__ __forceinline__ int row_read(int gy, int ny, int periodic) {
-  if (periodic) return wrap_periodic(gy, ny);
-  if (gy < 0) gy = -1 - gy;
-  if (gy >= ny) gy = 2 * ny - 1 - gy;
-  return gy < 0 ? 0 : (gy >= ny ? ny - 1 : gy);
-}
 
 template <int TX, int TY, int NH>
 struct Smem {
@@ -60,10 +42,8 @@ struct Smem {
   float mu[NH][N2], dmu[NH][N2];
   float p[N2], ux[N2], uy[N2];
   float gCx[NH][N2], gCy[NH][N2], grx[N2], gry[N2];
-  // R1: post-collision h*, g^eq + forcing (pass A -> pass B of stage 2) and
-  // the diffusion sources
+  // R1: post-collision h* and the diffusion sources
   float hs[NH][9][N1];
-  float eqf[9][N1];
   float sv[NH][N1];
 };
 
@@ -74,28 +54,14 @@ __device__ __forceinline__ int i2(int lx, int ly) { return (ly + 2) * (TX + 4) +
 template <int TX>
 __device__ __forceinline__ int i1(int lx, int ly) { return (ly + 1) * (TX + 2) + (lx + 1); }
 
-// FP16 deviation codec of the FORM 2 state (below).  One rounding order for
-// every encoder and decoder, so that a decode-encode round trip is exact.
-__device__ __forceinline__ float g16_decode(float Pref, __half d, int a, float inv_scale) {
-  return __fmaf_rn(wt(a), Pref, __half2float(d) * inv_scale);
-}
-__device__ __forceinline__ __half g16_encode(float g, float Pref, int a, float scale) {
-  return __float2half_rn(__fmaf_rn(-wt(a), Pref, g) * scale);
-}
-__device__ __forceinline__ float g16_reference(const float (&g)[9]) {
-  float Pn = 0.f;
-#pragma unroll
-  for (int a = 0; a < 9; ++a) Pn += g[a];
-  return Pn;
-}
-
 }  // namespace
 
 // FORM 0: the state holds the populations h^i (the method's state).
 // FORM 1: the state holds C_i only.  With tau_h = 1/2 the collision of Eq. 18
 // depends on h only through C_i = sum_a h_a^i, so C_i(t+1) = sum_a h_a^i(t+1)
 // carries the same information (same results up to the order of the FP32
-// sums) at 88 instead of 152 bytes per node-step.
+// sums) at 88 instead of 152 bytes per node-step; the destination-side term
+// then sums to S_i / 2 because the Gamma_a sum to one.
 // FORM 2: as FORM 1, and g is stored as FP16 deviations from a per-node
 // reference: d_a = (g_a - w_a P) * scale with P = sum_a g_a kept in FP32 (the
 // pressure-sized part stays in FP32, only the small deviations go to FP16),
@@ -115,22 +81,11 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
   for (int q = tid; q < S::N3; q += NT) {
     const int lx = q % S::W3 - 3, ly = q / S::W3 - 3;
     const long long k = (long long)row_read(y0 + ly, ny, per) * pitch + wrap_periodic(x0 + lx, nx);
-    float c[3] = {0.f, 0.f, 0.f};
+    float c[NH];
+    load_order_parameters<NH, FORM>(B, plane, k, c);
 #pragma unroll
-    for (int i = 0; i < NH; ++i) {
-      float acc;
-      if constexpr (FORM == 0) {
-        acc = 0.f;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) acc += B.h_in[((long long)i * 9 + a) * plane + k];
-      } else {
-        acc = B.h_in[(long long)i * plane + k];
-      }
-      c[i] = acc;
-      s.C[i][q] = acc;
-    }
-    c[2] = 1.0f - c[0] - c[1];
-    s.rho[q] = rho_of(P, c[0], c[1], c[2]);
+    for (int i = 0; i < NH; ++i) s.C[i][q] = c[i];
+    s.rho[q] = node_rho<NH>(P, c);
   }
   __syncthreads();
 
@@ -140,74 +95,32 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
     const int gy = y0 + ly;
     if (!per && (gy < 0 || gy >= ny)) continue;
     const long long k = (long long)(per ? wrap_periodic(gy, ny) : gy) * pitch + wrap_periodic(x0 + lx, nx);
-    float m0 = 0.f, mx = 0.f, my = 0.f;
-    float Pref = 0.f;
-    if constexpr (FORM == 2) Pref = B.g_in[(9 * plane) / 2 + k];
+    float g[9];
+    load_populations<FORM>(P, B, plane, k, g);
+    float cn[NH][9], rn[9];
+    const int c0 = i3<TX>(lx, ly);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      float ga;
-      if constexpr (FORM == 2) {
-        const __half *gh = reinterpret_cast<const __half *>(B.g_in);
-        ga = g16_decode(Pref, gh[(long long)a * plane + k], a, P.g16_inv_scale);
-      } else {
-        ga = B.g_in[(long long)a * plane + k];
-      }
-      s.g[a][q] = ga;
-      m0 += ga;
-      mx += ex(a) * ga;
-      my += ey(a) * ga;
+      const int j3 = c0 + ey(a) * S::W3 + ex(a);
+      s.g[a][q] = g[a];
+#pragma unroll
+      for (int i = 0; i < NH; ++i) cn[i][a] = s.C[i][j3];
+      rn[a] = s.rho[j3];
     }
-    float C[3], lap[3], gx[3], gyv[3], mu[3];
-    float rx = 0.f, ry = 0.f;
-    {
-      const int c0 = i3<TX>(lx, ly);
-      float cc[3][9];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        const int j3 = c0 + ey(a) * S::W3 + ex(a);
-        cc[0][a] = s.C[0][j3];
-        cc[1][a] = NH == 2 ? s.C[NH - 1][j3] : 0.f;
-        cc[2][a] = 1.0f - cc[0][a] - cc[1][a];
-        const float r = s.rho[j3];
-        rx += wt(a) * ex(a) * r;
-        ry += wt(a) * ey(a) * r;
-      }
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        float sx = 0.f, sy = 0.f, lp = 0.f;
-#pragma unroll
-        for (int a = 1; a < 9; ++a) {
-          sx += wt(a) * ex(a) * cc[j][a];
-          sy += wt(a) * ey(a) * cc[j][a];
-          lp += wt(a) * (cc[j][a] - cc[j][0]);
-        }
-        C[j] = cc[j][0];
-        gx[j] = 3.0f * sx;
-        gyv[j] = 3.0f * sy;
-        lap[j] = 6.0f * lp;
-      }
-    }
-    rx *= 3.0f;
-    ry *= 3.0f;
-    chem_potentials(P, C, lap, mu);
-    const float Fsx = mu[0] * gx[0] + mu[1] * gx[1] + mu[2] * gx[2];
-    const float Fsy = mu[0] * gyv[0] + mu[1] * gyv[1] + mu[2] * gyv[2];
-    const float rho = s.rho[i3<TX>(lx, ly)];
-    const float irho = 1.0f / rho;
-    const float ux = (3.0f * mx + 0.5f * (Fsx + P.force_x)) * irho;
-    const float uy = (3.0f * my + 0.5f * (Fsy - rho * P.gravity)) * irho;
+    NodeFields f;
+    node_fields<NH>(P, g, cn, rn, f);
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
-      s.mu[i][q] = mu[i];
-      s.dmu[i][q] = mu[i] - mu[2];
-      s.gCx[i][q] = gx[i];
-      s.gCy[i][q] = gyv[i];
+      s.mu[i][q] = f.mu[i];
+      s.dmu[i][q] = f.mu[i] - f.mu[2];
+      s.gCx[i][q] = f.gCx[i];
+      s.gCy[i][q] = f.gCy[i];
     }
-    s.p[q] = m0 + 0.5f * kCs2 * (ux * rx + uy * ry);
-    s.ux[q] = ux;
-    s.uy[q] = uy;
-    s.grx[q] = rx;
-    s.gry[q] = ry;
+    s.p[q] = f.p;
+    s.ux[q] = f.ux;
+    s.uy[q] = f.uy;
+    s.grx[q] = f.rx;
+    s.gry[q] = f.ry;
   }
   __syncthreads();
   if (!per && (y0 < 2 || y0 + TY + 2 > ny)) {
@@ -234,120 +147,44 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
     const long long k = (long long)(per ? wrap_periodic(gy, ny) : gy) * pitch + wrap_periodic(x0 + lx, nx);
     const int c2 = i2<TX>(lx, ly);
     const int c3 = i3<TX>(lx, ly);
-    const float ux = s.ux[c2], uy = s.uy[c2], p = s.p[c2], rho = s.rho[c3];
-    const float irho = 1.0f / rho;
-    // neighbour values, loaded once: p (2-ring), rho and C (3-ring)
-    float pn[9], rn[9], cn[NH][9];
+    float pn[9], rn[9], cn[NH][9], mun[NH][9], g[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const int j2 = c2 + ey(a) * S::W2 + ex(a), j3 = c3 + ey(a) * S::W3 + ex(a);
       pn[a] = s.p[j2];
       rn[a] = s.rho[j3];
-#pragma unroll
-      for (int i = 0; i < NH; ++i) cn[i][a] = s.C[i][j3];
-    }
-    // gradients of p and mu on R2
-    float px = 0.f, py = 0.f, mgx[NH], mgy[NH], mlap[NH];
-#pragma unroll
-    for (int i = 0; i < NH; ++i) mgx[i] = mgy[i] = mlap[i] = 0.f;
-#pragma unroll
-    for (int a = 1; a < 9; ++a) {
-      const int j2 = c2 + ey(a) * S::W2 + ex(a);
-      const float pv = pn[a];
-      px += wt(a) * ex(a) * pv;
-      py += wt(a) * ey(a) * pv;
+      g[a] = s.g[a][c2];
 #pragma unroll
       for (int i = 0; i < NH; ++i) {
-        const float m = s.mu[i][j2];
-        mgx[i] += wt(a) * ex(a) * m;
-        mgy[i] += wt(a) * ey(a) * m;
-        mlap[i] += wt(a) * (m - s.mu[i][c2]);
+        cn[i][a] = s.C[i][j3];
+        mun[i][a] = s.mu[i][j2];
       }
     }
-    px *= 3.0f;
-    py *= 3.0f;
-    float Fsx = 0.f, Fsy = 0.f, Cc[NH], sv[NH], kap[NH], udC[NH], dmu[NH];
+    NodeCenter c;
+    c.ux = s.ux[c2];
+    c.uy = s.uy[c2];
+    c.p = pn[0];
+    c.rho = rn[0];
+    c.grx = s.grx[c2];
+    c.gry = s.gry[c2];
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
-      dmu[i] = s.dmu[i][c2];
-      const float gcx = s.gCx[i][c2], gcy = s.gCy[i][c2];
-      Fsx += dmu[i] * gcx;
-      Fsy += dmu[i] * gcy;
-      Cc[i] = s.C[i][c3];
-      const float D0s = P.d0_sig[i];
-      const float lapmu = 6.0f * mlap[i];
-      if (P.mobility == 1)
-        sv[i] = D0s * Cc[i] * (1.0f - Cc[i]) * lapmu +
-                D0s * (1.0f - 2.0f * Cc[i]) * 3.0f * (gcx * mgx[i] + gcy * mgy[i]);
-      else
-        sv[i] = D0s * lapmu;
-      kap[i] = 3.0f * Cc[i] * irho;  // C_i / (rho cs^2)
-      udC[i] = ux * gcx + uy * gcy;
-      s.sv[i][q] = sv[i];
+      c.dmu[i] = s.dmu[i][c2];
+      c.gCx[i] = s.gCx[i][c2];
+      c.gCy[i] = s.gCy[i][c2];
     }
-    const float Fby = -rho * P.gravity;
-    const float udr = ux * s.grx[c2] + uy * s.gry[c2];
-    const float udFs = ux * Fsx + uy * Fsy;
-    const float udFb = ux * P.force_x + uy * Fby;
-    const float udp = ux * px + uy * py;
-    const float uu = ux * ux + uy * uy;
-    const float rcs2 = rho * kCs2;
-    // pass A: equilibria and forcing of every direction, h*, momentum flux;
-    // g - g^eq is written over g and g^eq + forcing kept for pass B
-    float Pxx = 0.f, Pyy = 0.f, Pxy = 0.f;
+    float hs[NH][9], sv[NH], tn, gd;
+    node_collide<NH>(P, c, pn, rn, cn, mun, g, B.tau_in[k], hs, sv, tn, gd);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const float exa = (float)ex(a), eya = (float)ey(a), w = wt(a);
-      const float eu = exa * ux + eya * uy;
-      const float G = w * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-      // directional derivatives from the neighbour registers (x + e_a, x - e_a)
-      const float dr = 0.5f * (rn[a] - rn[opp(a)]);
-      const float dp = 0.5f * (pn[a] - pn[opp(a)]);
-      float dC[NH];
-      float eFs = -udFs;
+      s.g[a][c2] = g[a];
 #pragma unroll
-      for (int i = 0; i < NH; ++i) {
-        dC[i] = 0.5f * (cn[i][a] - cn[i][opp(a)]);
-        eFs += dmu[i] * dC[i];
-      }
-      const float eFb = exa * P.force_x + eya * Fby - udFb;
-      const float ph = (dr - udr) * kCs2 * (G - w) + (eFs + eFb) * G;
-      const float geq = w * p + rcs2 * (G - w) - 0.5f * ph;
-      const float fneq = s.g[a][c2] - geq;
-      s.g[a][c2] = fneq;
-      s.eqf[a][q] = geq + ph;
-      Pxx += fneq * exa * exa;
-      Pyy += fneq * eya * eya;
-      Pxy += fneq * exa * eya;
-      const float ep = dp - udp - eFs - eFb;
-#pragma unroll
-      for (int i = 0; i < NH; ++i) {
-        const float phh = (dC[i] - udC[i] - kap[i] * ep) * G;
-        s.hs[i][a][q] = Cc[i] * G + 0.5f * phh + 0.5f * sv[i] * G;
-      }
+      for (int i = 0; i < NH; ++i) s.hs[i][a][q] = hs[i][a];
     }
-    // strain rate with the previous tau (R23) and the new tau (Eq. 31-33, R4)
-    const float tp = B.tau_in[k];
-    // (1/cs^2) (2 tau / (2 tau + 1)) / (2 tau rho cs^2) = 9 / ((2 tau + 1) rho)
-    const float fac = 9.0f * irho / (2.0f * tp + 1.0f);
-    const float Dxx = -fac * Pxx, Dyy = -fac * Pyy, Dxy = -fac * Pxy;
-    const float gd = sqrtf(2.0f * (Dxx * Dxx + Dyy * Dyy + 2.0f * Dxy * Dxy));
-    const float C3 = 1.0f - Cc[0] - (NH == 2 ? Cc[NH - 1] : 0.f);
-    const float tau1 = P.powerlaw ? tau_powerlaw(P, gd, irho) : P.tau[0];
-    const float tn = tau_mix(P, Cc[0], NH == 2 ? Cc[NH - 1] : 0.f, C3, tau1);
-    const float om = 1.0f / (tn + 0.5f);
-    // pass B: g* = g - om (g - g^eq) + forcing, over g in shared memory
 #pragma unroll
-    for (int a = 0; a < 9; ++a) s.g[a][c2] = (1.0f - om) * s.g[a][c2] + s.eqf[a][q];
-    if (lx >= 0 && lx < TX && ly >= 0 && ly < TY && x0 + lx < nx && gy < ny) {
-      B.tau_out[k] = tn;
-      if (B.shear) B.shear[k] = gd;
-      if (B.SV) {
-#pragma unroll
-        for (int i = 0; i < NH; ++i) B.SV[(long long)i * plane + k] = sv[i];
-      }
-      if (!(isfinite(tn) && isfinite(p) && isfinite(ux) && isfinite(uy))) atomicOr(B.err, 1u);
-    }
+    for (int i = 0; i < NH; ++i) s.sv[i][q] = sv[i];
+    if (lx >= 0 && lx < TX && ly >= 0 && ly < TY && x0 + lx < nx && gy < ny)
+      store_diagnostics<NH>(B, plane, k, tn, gd, sv, c);
   }
   __syncthreads();
 
@@ -358,15 +195,9 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
   if (x >= nx || y >= ny) return;
   const long long ky = (long long)y * pitch + x;
   const int yc1 = i1<TX>(tx, ty), yc2 = i2<TX>(tx, ty);
-  const float uxy = s.ux[yc2], uyy = s.uy[yc2];
-  const float uuy = uxy * uxy + uyy * uyy;
-  float svy[NH], csum[NH];
+  float gy[9], hy[NH][9], svy[NH];
 #pragma unroll
-  for (int i = 0; i < NH; ++i) {
-    svy[i] = 0.5f * s.sv[i][yc1];
-    csum[i] = 0.f;
-  }
-  float gy[9];
+  for (int i = 0; i < NH; ++i) svy[i] = s.sv[i][yc1];
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     int s1 = yc1 - ey(a) * S::W1 - ex(a);
@@ -380,34 +211,11 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
         b = opp(a);
       }
     }
-    if constexpr (FORM == 2) {
-      gy[a] = s.g[b][s2];
-    } else {
-      B.g_out[(long long)a * plane + ky] = s.g[b][s2];
-    }
-    const float euy = ex(a) * uxy + ey(a) * uyy;
-    const float Gy = wt(a) * (1.0f + 3.0f * euy + 4.5f * euy * euy - 1.5f * uuy);
+    gy[a] = s.g[b][s2];
 #pragma unroll
-    for (int i = 0; i < NH; ++i) {
-      const float hv = s.hs[i][b][s1] + svy[i] * Gy;
-      if constexpr (FORM == 0) {
-        B.h_out[((long long)i * 9 + a) * plane + ky] = hv;
-      } else {
-        csum[i] += hv;
-      }
-    }
+    for (int i = 0; i < NH; ++i) hy[i][a] = s.hs[i][b][s1];
   }
-  if constexpr (FORM != 0) {
-#pragma unroll
-    for (int i = 0; i < NH; ++i) B.h_out[(long long)i * plane + ky] = csum[i];
-  }
-  if constexpr (FORM == 2) {
-    const float Pn = g16_reference(gy);
-    B.g_out[(9 * plane) / 2 + ky] = Pn;
-    __half *gh = reinterpret_cast<__half *>(B.g_out);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) gh[(long long)a * plane + ky] = g16_encode(gy[a], Pn, a, P.g16_scale);
-  }
+  store_node<NH, FORM>(P, B, plane, ky, gy, hy, svy, s.ux[yc2], s.uy[yc2]);
 }
 
 // One lattice: tile (blockIdx.x, blockIdx.y).
@@ -530,19 +338,28 @@ struct VariantTable {
 
 static int form_of(const DevParams &P) { return P.g16 ? 2 : (P.collapse_h ? 1 : 0); }
 
-int fused_variant_count(const DevParams &P) {
+int tile_variant_count(const DevParams &P) {
   if (form_of(P) == 2) return P.nh == 1 ? VariantTable<1, 2>::kCount : VariantTable<2, 2>::kCount;
   return P.nh == 1 ? VariantTable<1, 0>::kCount : VariantTable<2, 0>::kCount;
 }
 
+// Configurations 0 .. sweep_variant_count - 1 are row sweeps, the rest tiles.
+int fused_variant_count(const DevParams &P) { return sweep_variant_count(P) + tile_variant_count(P); }
+
 const char *fused_variant_name(const DevParams &P, int v) {
   if (v < 0 || v >= fused_variant_count(P)) v = 0;
+  const int ns = sweep_variant_count(P);
+  if (v < ns) return sweep_variant_name(P, v);
+  v -= ns;
   if (form_of(P) == 2) return P.nh == 1 ? VariantTable<1, 2>::name(v) : VariantTable<2, 2>::name(v);
   return P.nh == 1 ? VariantTable<1, 0>::name(v) : VariantTable<2, 0>::name(v);
 }
 
 cudaError_t launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v) {
   if (v < 0 || v >= fused_variant_count(P)) v = 0;
+  const int ns = sweep_variant_count(P);
+  if (v < ns) return launch_sweep_step(P, B, s, v);
+  v -= ns;
   switch (form_of(P)) {
     case 2: return P.nh == 1 ? VariantTable<1, 2>::launch(v, P, B, s) : VariantTable<2, 2>::launch(v, P, B, s);
     case 1: return P.nh == 1 ? VariantTable<1, 1>::launch(v, P, B, s) : VariantTable<2, 1>::launch(v, P, B, s);
@@ -550,16 +367,17 @@ cudaError_t launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStr
   }
 }
 
-void fused_variant_tile(const DevParams &P, int v, int *tx, int *ty) {
-  if (v < 0 || v >= fused_variant_count(P)) v = 0;
-  if (P.nh == 1) VariantTable<1, 0>::tile(v, tx, ty);
+int batched_variant_count(int nh) { return nh == 1 ? VariantTable<1, 0>::kCount : VariantTable<2, 0>::kCount; }
+
+void batched_variant_tile(int nh, int v, int *tx, int *ty) {
+  if (v < 0 || v >= batched_variant_count(nh)) v = 0;
+  if (nh == 1) VariantTable<1, 0>::tile(v, tx, ty);
   else VariantTable<2, 0>::tile(v, tx, ty);
 }
 
 cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
                                 int parity, cudaStream_t s, int v) {
-  const int count = nh == 1 ? VariantTable<1, 0>::kCount : VariantTable<2, 0>::kCount;
-  if (v < 0 || v >= count) v = 0;
+  if (v < 0 || v >= batched_variant_count(nh)) v = 0;
   if (collapse_h) {
     if (nh == 1) return VariantTable<1, 1>::launch_batched(v, cases, work, nwork, parity, s);
     return VariantTable<2, 1>::launch_batched(v, cases, work, nwork, parity, s);

@@ -42,10 +42,16 @@ struct WorkItem {
 };
 
 bool fused_supported(const DevParams &P);
-void fused_variant_tile(const DevParams &P, int v, int *tx, int *ty);
+// Tile configurations of the batched step (work items are (case, tile)).
+int batched_variant_count(int nh);
+void batched_variant_tile(int nh, int v, int *tx, int *ty);
 cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
                                 int parity, cudaStream_t s, int v);
-// Launch configurations of the fused step (tile, threads, CTAs per SM).
+// Launch configurations of the fused step: row sweeps (strip width, rows per
+// pipeline step, threads, CTAs per SM), then tiles (tile, threads, CTAs per SM).
+int sweep_variant_count(const DevParams &P);
+const char *sweep_variant_name(const DevParams &P, int v);
+cudaError_t launch_sweep_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v);
 int fused_variant_count(const DevParams &P);
 const char *fused_variant_name(const DevParams &P, int v);
 cudaError_t launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v);

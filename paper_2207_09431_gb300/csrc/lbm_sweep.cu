@@ -1,0 +1,322 @@
+// Row-sweep form of the fused coupled D2Q9 step (arXiv 2207.09431, Sec.
+// 2.2-2.3): one kernel per time step, pull scheme, the same per-node
+// arithmetic as the tile form (lbm_node.cuh).
+//
+// A CTA owns a strip of TX columns and a segment of rows and walks up the
+// segment RS rows per pipeline step.  The four stages of the step run skewed
+// by one pipeline step each, so that within a step no stage reads what
+// another stage writes in the same step and a single barrier per step
+// suffices:
+//   stage 0  C and rho                      rows [j + 3RS + 3, j + 4RS + 3)
+//   stage 1  mu, p, u, isotropic gradients   rows [j + 2RS + 2, j + 3RS + 2)
+//   stage 2  collision (h*, tau, g*)         rows [j + RS + 1,  j + 2RS + 1)
+//   stage 3  streaming of output rows        rows [j, j + RS)
+// Every stage reads rows that earlier steps produced (stage 1 needs C one row
+// beyond its own, stage 2 needs mu and p one row beyond, stage 3 the
+// collision one row beyond).  Each quantity lives in a shared-memory ring
+// indexed by row, deep enough for the rows alive at once.  A node's stage
+// 0-2 work is done once per segment instead of once per overlapping tile
+// halo: the halo is recomputed only across strip edges (3, 2, 1 columns per
+// side) and at segment ends (3, 2, 1 rows per end).
+//
+// Each thread owns one item of every stage (NT >= RS (TX + 6)), with its
+// column fixed for the whole sweep.  The global loads of a step (state of
+// stage 0, g of stage 1, previous tau of stage 2) are issued first and used
+// last, after stage 3 and the collision, so their latency overlaps the
+// step's shared-memory work.
+//
+// Ghost rows beyond a wall (reading R10): stage 0 loads mirrored rows;
+// stencils of mu and p in stage 2 read the mirror row, which is the centre
+// row itself for the one-row reach of those stencils; stage 3 bounces back.
+#include <cuda_fp16.h>
+
+#include "lbm_kernels.h"
+#include "lbm_node.cuh"
+
+namespace lbm {
+
+namespace {
+
+template <int TX, int RS, int NH>
+struct PipeSmem {
+  static constexpr int W3 = TX + 6, W2 = TX + 4, W1 = TX + 2;
+  // ring depths: rows alive at once (written this step or read this step)
+  static constexpr int D3 = 3 * RS + 3, D2 = 2 * RS + 2, DA = 2 * RS + 1, DB = 2 * RS + 2;
+  float C[NH][D3][W3];
+  float rho[D3][W3];
+  float mu[NH][D2][W2];
+  float p[D2][W2];
+  // stage 1 -> stage 2 (1-ring columns): g and the fields the collision
+  // needs at its own node
+  float g[9][DA][W1];
+  float ux[DA][W1], uy[DA][W1];
+  float dmu[NH][DA][W1], gCx[NH][DA][W1], gCy[NH][DA][W1];
+  float grx[DA][W1], gry[DA][W1];
+  // stage 2 -> stage 3: g*, h*, sources and the velocity of the node
+  float gs[9][DB][W1];
+  float hs[NH][9][DB][W1];
+  float sv[NH][DB][W1];
+  float uxb[DB][W1], uyb[DB][W1];
+};
+
+template <int D>
+__device__ __forceinline__ int slot(int r, int base) {
+  return (int)((unsigned)(r - base) % (unsigned)D);
+}
+
+template <int TX, int RS, int NH, int FORM, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffers B, int seg_len) {
+  using S = PipeSmem<TX, RS, NH>;
+  static_assert(NT >= RS * S::W3, "one item of every stage per thread");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S &s = *reinterpret_cast<S *>(smem_raw);
+  const int nx = P.nx, ny = P.ny, per = P.periodic_y, pitch = P.pitch;
+  const long long plane = P.plane;
+  const int x0 = blockIdx.x * TX;
+  const int ys = blockIdx.y * seg_len;
+  const int ye = min(ys + seg_len, ny);
+  const int t = threadIdx.x;
+
+  // this thread's item of each stage: row offset within the step, column
+  const bool v0 = t < RS * S::W3, v1 = t < RS * S::W2, v2 = t < RS * S::W1, v3 = t < RS * TX;
+  const int d0 = t / S::W3, c0 = t % S::W3;
+  const int d1 = t / S::W2, c1 = t % S::W2;
+  const int d2 = t / S::W1, c2 = t % S::W1;
+  const int d3 = t / TX, c3 = t % TX;
+  const int x0c = wrap_periodic(x0 - 3 + c0, nx);
+  const int x1c = wrap_periodic(x0 - 2 + c1, nx);
+  const int x2 = x0 - 1 + c2, x2c = wrap_periodic(x2, nx);
+  const int x3 = x0 + c3;
+  const bool own2 = c2 >= 1 && c2 <= TX && x2 < nx;
+  const bool out3 = v3 && x3 < nx;
+
+  // first step: stage 0 starts at row ys - 3, and j stays aligned with ys
+  const int j0 = ys - 3 * RS - RS * ((6 + RS - 1) / RS);
+  const int base = j0;  // ring rows are counted from here (all rows used are >= base)
+
+  for (int j = j0; j < ye; j += RS) {
+    // ---- issue this step's global loads
+    const int r0 = j + 3 * RS + 3 + d0;
+    const int r1 = j + 2 * RS + 2 + d1;
+    const int r2 = j + RS + 1 + d2;
+    const int r3 = j + d3;
+    const bool a0 = v0 && r0 >= ys - 3 && r0 < ye + 3;
+    const bool a1 = v1 && r1 >= ys - 2 && r1 < ye + 2 && (per || (r1 >= 0 && r1 < ny));
+    const bool a2 = v2 && r2 >= ys - 1 && r2 < ye + 1 && (per || (r2 >= 0 && r2 < ny));
+    const bool a3 = out3 && r3 >= ys && r3 < ye;
+    float cst[NH];
+    if (a0) load_order_parameters<NH, FORM>(B, plane, (long long)row_read(r0, ny, per) * pitch + x0c, cst);
+    float gv[9];
+    const long long k1 = (long long)(per ? wrap_periodic(r1, ny) : r1) * pitch + x1c;
+    if (a1) load_populations<FORM>(P, B, plane, k1, gv);
+    const long long k2 = (long long)(per ? wrap_periodic(r2, ny) : r2) * pitch + x2c;
+    const float tprev = a2 ? B.tau_in[k2] : 0.f;
+
+    // ---- stage 3: arriving populations of output row r3
+    if (a3) {
+      const int sb = slot<S::DB>(r3, base);
+      float gy[9], hy[NH][9], svy[NH];
+#pragma unroll
+      for (int q = 0; q < NH; ++q) svy[q] = s.sv[q][sb][c3 + 1];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        int src = r3 - ey(a), cs = c3 + 1 - ex(a), b = a;
+        if (!per && (src < 0 || src >= ny)) {  // half-way bounce-back: the population left r3 in -e_a
+          src = r3;
+          cs = c3 + 1;
+          b = opp(a);
+        }
+        const int ss = slot<S::DB>(src, base);
+        gy[a] = s.gs[b][ss][cs];
+#pragma unroll
+        for (int q = 0; q < NH; ++q) hy[q][a] = s.hs[q][b][ss][cs];
+      }
+      store_node<NH, FORM>(P, B, plane, (long long)r3 * pitch + x3, gy, hy, svy, s.uxb[sb][c3 + 1],
+                           s.uyb[sb][c3 + 1]);
+    }
+
+    // ---- stage 2: collision of row r2 (1-ring column c2)
+    if (a2) {
+      const int sa = slot<S::DA>(r2, base), sb = slot<S::DB>(r2, base);
+      float pn[9], rn[9], cn[NH][9], mun[NH][9], g2[9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        // mu and p one row beyond a wall: the mirror row is row r2 itself
+        int rm = r2 + ey(a);
+        if (!per) rm = rm < 0 ? 0 : (rm >= ny ? ny - 1 : rm);
+        const int sm = slot<S::D2>(rm, base);
+        const int sc = slot<S::D3>(r2 + ey(a), base);
+        pn[a] = s.p[sm][c2 + 1 + ex(a)];
+        rn[a] = s.rho[sc][c2 + 2 + ex(a)];
+        g2[a] = s.g[a][sa][c2];
+#pragma unroll
+        for (int q = 0; q < NH; ++q) {
+          cn[q][a] = s.C[q][sc][c2 + 2 + ex(a)];
+          mun[q][a] = s.mu[q][sm][c2 + 1 + ex(a)];
+        }
+      }
+      NodeCenter nc;
+      nc.ux = s.ux[sa][c2];
+      nc.uy = s.uy[sa][c2];
+      nc.p = pn[0];
+      nc.rho = rn[0];
+      nc.grx = s.grx[sa][c2];
+      nc.gry = s.gry[sa][c2];
+#pragma unroll
+      for (int q = 0; q < NH; ++q) {
+        nc.dmu[q] = s.dmu[q][sa][c2];
+        nc.gCx[q] = s.gCx[q][sa][c2];
+        nc.gCy[q] = s.gCy[q][sa][c2];
+      }
+      float hs[NH][9], sv[NH], tn, gd;
+      node_collide<NH>(P, nc, pn, rn, cn, mun, g2, tprev, hs, sv, tn, gd);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        s.gs[a][sb][c2] = g2[a];
+#pragma unroll
+        for (int q = 0; q < NH; ++q) s.hs[q][a][sb][c2] = hs[q][a];
+      }
+#pragma unroll
+      for (int q = 0; q < NH; ++q) s.sv[q][sb][c2] = sv[q];
+      s.uxb[sb][c2] = nc.ux;
+      s.uyb[sb][c2] = nc.uy;
+      if (own2 && r2 >= ys && r2 < ye) store_diagnostics<NH>(B, plane, k2, tn, gd, sv, nc);
+    }
+
+    // ---- stage 1: fields of row r1 (2-ring column c1)
+    if (a1) {
+      float cn[NH][9], rn[9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        const int sc = slot<S::D3>(r1 + ey(a), base);
+#pragma unroll
+        for (int q = 0; q < NH; ++q) cn[q][a] = s.C[q][sc][c1 + 1 + ex(a)];
+        rn[a] = s.rho[sc][c1 + 1 + ex(a)];
+      }
+      NodeFields f;
+      node_fields<NH>(P, gv, cn, rn, f);
+      const int sm = slot<S::D2>(r1, base);
+#pragma unroll
+      for (int q = 0; q < NH; ++q) s.mu[q][sm][c1] = f.mu[q];
+      s.p[sm][c1] = f.p;
+      if (c1 >= 1 && c1 <= TX + 2) {
+        const int sa = slot<S::DA>(r1, base), cc = c1 - 1;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) s.g[a][sa][cc] = gv[a];
+#pragma unroll
+        for (int q = 0; q < NH; ++q) {
+          s.dmu[q][sa][cc] = f.mu[q] - f.mu[2];
+          s.gCx[q][sa][cc] = f.gCx[q];
+          s.gCy[q][sa][cc] = f.gCy[q];
+        }
+        s.ux[sa][cc] = f.ux;
+        s.uy[sa][cc] = f.uy;
+        s.grx[sa][cc] = f.rx;
+        s.gry[sa][cc] = f.ry;
+      }
+    }
+
+    // ---- stage 0: C and rho of row r0 (3-ring column c0)
+    if (a0) {
+      const int sc = slot<S::D3>(r0, base);
+#pragma unroll
+      for (int q = 0; q < NH; ++q) s.C[q][sc][c0] = cst[q];
+      s.rho[sc][c0] = node_rho<NH>(P, cst);
+    }
+    __syncthreads();
+  }
+}
+
+// Segment length for a strip count: balances the waves of CTAs against the
+// per-segment overhead (3 + 2 + 1 extra rows of stages 0-2 at each end and
+// the steps that fill the pipeline).
+int choose_segment(int ny, int strips, int resident, int rs) {
+  int best_len = ny;
+  double best_eff = -1.0;
+  for (int len = rs; len <= 1024; len += rs) {
+    const int nseg = (ny + len - 1) / len;
+    const long long total = (long long)strips * nseg;
+    const long long waves = (total + resident - 1) / resident;
+    const double fill = (double)total / (double)(waves * resident);
+    const double eff = fill * (double)len / (double)(len + 6 + rs);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best_len = len;
+    }
+    if (len >= ny) break;
+  }
+  return best_len;
+}
+
+template <int TX, int RS, int NH, int FORM, int NT, int MINB>
+cudaError_t launch_sweep_t(const DevParams &P, const FusedBuffers &B, cudaStream_t st) {
+  const size_t smem = sizeof(PipeSmem<TX, RS, NH>);
+  static bool configured = false;
+  static int resident_per_sm = 0, sms = 0;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_step_sweep<TX, RS, NH, FORM, NT, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident_per_sm, k_step_sweep<TX, RS, NH, FORM, NT, MINB>,
+                                                        NT, smem);
+    if (e != cudaSuccess) return e;
+    if (resident_per_sm < 1) return cudaErrorInvalidConfiguration;
+    configured = true;
+  }
+  const int strips = (P.nx + TX - 1) / TX;
+  const int len = choose_segment(P.ny, strips, resident_per_sm * sms, RS);
+  const dim3 grd(strips, (P.ny + len - 1) / len);
+  k_step_sweep<TX, RS, NH, FORM, NT, MINB><<<grd, NT, smem, st>>>(P, B, len);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Launch configurations of the row sweep: strip width x rows per pipeline
+// step / threads / minimum resident CTAs per SM.
+int sweep_variant_count(const DevParams &P) { return P.nh == 1 ? 5 : 3; }
+
+const char *sweep_variant_name(const DevParams &P, int v) {
+  static const char *n1[5] = {"64x2/160/3", "32x4/160/3", "128x1/160/2", "64x4/288/2", "64x1/96/5"};
+  static const char *n2[3] = {"64x2/160/2", "32x4/160/2", "64x1/96/4"};
+  if (v < 0 || v >= sweep_variant_count(P)) v = 0;
+  return P.nh == 1 ? n1[v] : n2[v];
+}
+
+template <int NH, int FORM>
+static cudaError_t sweep_dispatch(int v, const DevParams &P, const FusedBuffers &B, cudaStream_t s) {
+  if constexpr (NH == 1) {
+    switch (v) {
+      case 1: return launch_sweep_t<32, 4, NH, FORM, 160, 3>(P, B, s);
+      case 2: return launch_sweep_t<128, 1, NH, FORM, 160, 2>(P, B, s);
+      case 3: return launch_sweep_t<64, 4, NH, FORM, 288, 2>(P, B, s);
+      case 4: return launch_sweep_t<64, 1, NH, FORM, 96, 5>(P, B, s);
+      default: return launch_sweep_t<64, 2, NH, FORM, 160, 3>(P, B, s);
+    }
+  } else {
+    switch (v) {
+      case 1: return launch_sweep_t<32, 4, NH, FORM, 160, 2>(P, B, s);
+      case 2: return launch_sweep_t<64, 1, NH, FORM, 96, 4>(P, B, s);
+      default: return launch_sweep_t<64, 2, NH, FORM, 160, 2>(P, B, s);
+    }
+  }
+}
+
+cudaError_t launch_sweep_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v) {
+  if (v < 0 || v >= sweep_variant_count(P)) v = 0;
+  const int form = P.g16 ? 2 : (P.collapse_h ? 1 : 0);
+  if (P.nh == 1) {
+    if (form == 2) return sweep_dispatch<1, 2>(v, P, B, s);
+    if (form == 1) return sweep_dispatch<1, 1>(v, P, B, s);
+    return sweep_dispatch<1, 0>(v, P, B, s);
+  }
+  if (form == 2) return sweep_dispatch<2, 2>(v, P, B, s);
+  if (form == 1) return sweep_dispatch<2, 1>(v, P, B, s);
+  return sweep_dispatch<2, 0>(v, P, B, s);
+}
+
+}  // namespace lbm

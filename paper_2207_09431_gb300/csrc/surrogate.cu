@@ -442,8 +442,9 @@ lbm_status surr_train(surr_net *n, const double *X, const double *Y, int rows, i
   return LBM_OK;
 }
 
-// Ensemble prediction: mean and spread (max - min over members) of the two
-// outputs in raw units, and flags for inputs outside the training box.
+// Ensemble prediction: mean and disagreement (largest deviation of a member
+// from the mean) of the two outputs in raw units, and flags for inputs outside
+// the training box.
 lbm_status surr_predict(surr_net *n, const double *X, int rows, double *y_mean, double *y_spread, int *outside) {
   if (!n || !X || !y_mean || rows < 1 || rows > n->max_batch) return LBM_E_INVAL;
   if (!n->trained) {
@@ -453,7 +454,7 @@ lbm_status surr_predict(surr_net *n, const double *X, int rows, double *y_mean, 
   std::vector<float> xs((size_t)rows * 5), y((size_t)rows * 2);
   for (int r = 0; r < rows; ++r)
     for (int c = 0; c < 5; ++c) xs[r * 5 + c] = (float)((X[r * 5 + c] - n->in_mean[c]) / n->in_std[c]);
-  std::vector<double> lo((size_t)rows * 2, 1e300), hi((size_t)rows * 2, -1e300), sum((size_t)rows * 2, 0.0);
+  std::vector<double> val((size_t)n->members * rows * 2), sum((size_t)rows * 2, 0.0);
   cudaError_t e = cudaSuccess;
   for (int mem = 0; mem < n->members && e == cudaSuccess; ++mem) {
     e = cudaMemcpyAsync(n->act[0], xs.data(), xs.size() * 4, cudaMemcpyHostToDevice, n->stream);
@@ -462,15 +463,17 @@ lbm_status surr_predict(surr_net *n, const double *X, int rows, double *y_mean, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
     for (int i = 0; e == cudaSuccess && i < rows * 2; ++i) {
       const double v = y[i] * n->out_std[i % 2] + n->out_mean[i % 2];
+      val[(size_t)mem * rows * 2 + i] = v;
       sum[i] += v;
-      lo[i] = v < lo[i] ? v : lo[i];
-      hi[i] = v > hi[i] ? v : hi[i];
     }
   }
   if (e != cudaSuccess) return n->cuda_fail(e, "surr_predict");
   for (int i = 0; i < rows * 2; ++i) {
     y_mean[i] = sum[i] / n->members;
-    if (y_spread) y_spread[i] = hi[i] - lo[i];
+    double dev = 0.0;
+    for (int mem = 0; mem < n->members; ++mem)
+      dev = std::fmax(dev, std::fabs(val[(size_t)mem * rows * 2 + i] - y_mean[i]));
+    if (y_spread) y_spread[i] = dev;
   }
   if (outside)
     for (int r = 0; r < rows; ++r) {

@@ -137,6 +137,33 @@ def paper_case(n=0.6, eotvos=10.0, density_ratio=1000.0, mobility=1, k=None):
     return p, [(L / 2.0, 0.6 * L, R, 3)]
 
 
+def paper_grid_cases(density_ratio=1000.0, mobility=0, fd_scheme=0, ns=(0.5, 0.6, 0.8, 1.0),
+                     eotvos=(1.0, 10.0, 50.0), log10_mo=(-3.0, -1.0, 1.0), L=200):
+    """The rising-bubble grid of Sec. 4.3 at the paper's size: L x 2L, d = L/4
+    at (L/2, 0.6 L), g from sqrt(g d) = 0.01, sigma from Eo, the power-law
+    consistency k from Mo = g drho / (rho_l^2 sigma^3) [k (U/d)^(n-1)]^4 with
+    U = sqrt(g d), gas relaxation time 0.5 (viscosity ratio k / eta_gas up to
+    about 1000).  Returns [(params, discs, meta)]."""
+    out = []
+    R = L / 8.0
+    d = 2.0 * R
+    g = 0.01 ** 2 / d
+    U = math.sqrt(g * d)
+    rho_g = 1.0 / density_ratio
+    drho = 1.0 - rho_g
+    for n in ns:
+        for Eo in eotvos:
+            for lm in log10_mo:
+                sigma = drho * g * d * d / Eo
+                k = (10.0 ** lm * sigma ** 3 / (g * drho)) ** 0.25 / (U / d) ** (n - 1.0)
+                p = rising_bubble_params(L, 2 * L, density_ratio=density_ratio, n=n, k=k, sigma=sigma,
+                                         gravity=g, mobility=mobility)
+                p["fd_scheme"] = fd_scheme
+                out.append((p, [(L / 2.0, 0.6 * L, R, 3)], dict(n=n, Eo=Eo, log10_Mo=lm, density_ratio=density_ratio,
+                                                               viscosity_ratio=k / (rho_g * p["tau"][2] / 3.0))))
+    return out
+
+
 def three_comp_case(nx=256, mobility=0, seed=0, max_draws=100000):
     """Three components, fully periodic: matrix 1 (power law n = 0.6), two droplets
     of component 2 (R = 20, 12 at nx = 256, scaled with nx) and a bubble of 3

@@ -1,7 +1,7 @@
 """Surrogate of the rising-bubble terminal state, with the solver as fallback.
 
 The network (CUDA kernels behind ``surr_*`` in include/lbm.h) maps
-(n, Eo, log10 Mo, density ratio, viscosity ratio) to (log U_t, log C_D).  Its
+(n, Eo, log10 Mo, density ratio, log10 viscosity ratio) to (log U_t, log C_D).  Its
 training data are terminal states computed by the batched lattice Boltzmann
 solver (``lbm_batch_*``); its answer is used only when the input lies inside
 the box of the training inputs and the ensemble agrees within ``max_spread``;
@@ -25,17 +25,22 @@ from . import inputs, lbm
 
 
 def features(params: dict, meta: dict) -> np.ndarray:
-    """(n, Eo, log10 Mo, density ratio, viscosity ratio k / eta_gas), with
-    eta_gas = rho_gas cs^2 tau_gas."""
+    """(n, Eo, log10 Mo, density ratio, log10 of the viscosity ratio
+    k / eta_gas), with eta_gas = rho_gas cs^2 tau_gas (k spans decades over
+    the Mo range)."""
     rho_l, rho_g = params["rho"][0], params["rho"][2]
     eta_g = rho_g * params["tau"][2] / 3.0
-    return np.array([meta["n"], meta["Eo"], meta["log10_Mo"], rho_l / rho_g, params["pl_k"] / eta_g])
+    return np.array([meta["n"], meta["Eo"], meta["log10_Mo"], rho_l / rho_g,
+                     math.log10(params["pl_k"] / eta_g)])
 
 
-def run_to_terminal(cases, window=1000, rtol=2e-3, max_steps=30000, stream=None, device="cuda"):
+def run_to_terminal(cases, window=2000, rtol=0.05, max_steps=40000, stream=None, device="cuda"):
     """Advances cases [(params, discs, meta), ...] together until each reaches
-    its terminal state.  Returns per-case dicts with U_t, C_D, steps,
-    converged, finite, and the wall time."""
+    its terminal state.  The rise velocity is measured as the centroid
+    displacement (Eq. 44) per window, i.e. the window average of Eq. 43, because
+    the instantaneous value oscillates with the bubble shape.  Returns per-case
+    dicts with U_t, C_D (Eq. 37, through lbm_postprocess), steps, converged and
+    finite, and the wall time."""
     batch = lbm.Batch([c[0] for c in cases], device=device, stream=stream)
     for i, (p, b, _) in enumerate(cases):
         batch.case(i).set_fields(inputs.bubble_fields(p["nx"], p["ny"], 2, p["xi"], b, seed=i, noise=1e-8))
@@ -43,7 +48,7 @@ def run_to_terminal(cases, window=1000, rtol=2e-3, max_steps=30000, stream=None,
     n = len(cases)
     done = [False] * n
     out = [dict(U_t=math.nan, C_D=math.nan, steps=0, converged=False, finite=True) for _ in range(n)]
-    hist = [[] for _ in range(n)]
+    ys = [[batch.case(i).observables()["centroid"][1]] for i in range(n)]
     t0 = time.perf_counter()
     steps = 0
     while steps < max_steps and not all(done):
@@ -57,19 +62,23 @@ def run_to_terminal(cases, window=1000, rtol=2e-3, max_steps=30000, stream=None,
             if done[i]:
                 continue
             ob = batch.case(i).observables()
-            v, y = ob["rise_velocity"], ob["centroid"][1]
-            if not (np.isfinite(v) and np.isfinite(y)):
+            y = ob["centroid"][1]
+            if not (np.isfinite(y) and np.isfinite(ob["rise_velocity"])):
                 out[i].update(finite=False, steps=steps)
                 done[i] = True
                 batch.set_active(i, False)
                 continue
-            hist[i].append(v)
+            ys[i].append(y)
+            u = np.diff(ys[i]) / window
             p = cases[i][0]
             top = p["ny"] - 1.5 * 2.0 * cases[i][1][0][2]
-            steady = (len(hist[i]) >= 3 and abs(hist[i][-1] - hist[i][-2]) < rtol * abs(hist[i][-1])
-                      and abs(hist[i][-2] - hist[i][-3]) < rtol * abs(hist[i][-2]))
+            steady = len(u) >= 3 and all(abs(u[-j] - u[-j - 1]) < rtol * abs(u[-j]) for j in (1, 2))
             if steady or y > top or steps >= max_steps:
-                out[i].update(U_t=v, C_D=ob["drag_coefficient"], steps=steps, converged=bool(steady or y > top))
+                raw = np.array(ob["raw"])
+                raw[10] = u[-1] * raw[6]           # window-averaged rise velocity
+                post = lbm.lbm_postprocess(p, raw)
+                out[i].update(U_t=float(u[-1]), C_D=post["drag_coefficient"], steps=steps,
+                              converged=bool(steady or y > top))
                 done[i] = True
                 batch.set_active(i, False)
     wall = time.perf_counter() - t0
@@ -89,10 +98,10 @@ class TerminalStateModel:
 
     def predict(self, X):
         """(U_t, C_D, trusted) per row: trusted means inside the training box
-        and an ensemble spread below max_spread in both outputs (relative)."""
+        and no member farther than max_spread from the ensemble mean in either
+        output (relative: the outputs are logarithms)."""
         mean, spread, outside = self.net.predict(np.asarray(X, dtype=np.float64))
         U, CD = np.exp(mean[:, 0]), np.exp(mean[:, 1])
-        # spread of log values = relative spread of the values
         trusted = (~outside) & (spread[:, 0] < self.max_spread) & (spread[:, 1] < self.max_spread)
         return U, CD, trusted
 
@@ -111,3 +120,45 @@ class TerminalStateModel:
                     U[i], CD[i] = res[j]["U_t"], res[j]["C_D"]
                     j += 1
         return U, CD, ~trusted, time.perf_counter() - t0
+
+
+def evaluate(n_train=1024, n_test=128, grid=(100, 200), members=5, epochs=1000, max_steps=30000, seed=1000,
+             test_seed=9000, stream=None, max_spread=0.05, return_model=False):
+    """Trains on solver terminal states of n_train seeded cases and judges the
+    network on n_test held-out cases solved in full.  Returns a summary dict:
+    C_D error of the network on every converged test case and on the trusted
+    ones, the fallback count, and the time to answer with and without the
+    network (and the trained model if return_model)."""
+    train = inputs.ensemble_cases(n_train, seed=seed, grids=(grid,))
+    res, wall_train = run_to_terminal(train, max_steps=max_steps, stream=stream)
+    keep = [i for i, r in enumerate(res) if r["finite"] and r["converged"] and r["U_t"] > 0 and r["C_D"] > 0]
+    X = np.stack([features(train[i][0], train[i][2]) for i in keep])
+    U = np.array([res[i]["U_t"] for i in keep])
+    CD = np.array([res[i]["C_D"] for i in keep])
+    model = TerminalStateModel(members=members, seed=seed, max_rows=max(len(keep), 1), max_batch=512,
+                               max_spread=max_spread)
+    loss = model.fit(X, U, CD, epochs=epochs)
+    test = inputs.ensemble_cases(n_test, seed=test_seed, grids=(grid,))
+    ref, wall_solver = run_to_terminal(test, max_steps=max_steps, stream=stream)
+    Xt = np.stack([features(p, m) for p, _, m in test])
+    t0 = time.perf_counter()
+    Up, CDp, trusted = model.predict(Xt)
+    wall_net = time.perf_counter() - t0
+    ok = np.array([r["finite"] and r["converged"] and r["U_t"] > 0 for r in ref])
+    judged = trusted & ok
+    cd_ref = np.array([r["C_D"] for r in ref])
+    err = np.abs(CDp[judged] / cd_ref[judged] - 1.0)
+    err_all = np.abs(CDp[ok] / cd_ref[ok] - 1.0)
+    summary = {
+        "train_cases": n_train, "train_converged": len(keep), "train_solver_s": round(wall_train, 2),
+        "final_loss": loss, "test_cases": n_test, "test_converged": int(ok.sum()),
+        "trusted": int(trusted.sum()), "judged": int(judged.sum()),
+        "cd_rel_err_median": float(np.median(err)) if err.size else None,
+        "cd_rel_err_p90": float(np.percentile(err, 90)) if err.size else None,
+        "cd_within_5pct": float(np.mean(err < 0.05)) if err.size else None,
+        "cd_rel_err_median_all_converged": float(np.median(err_all)) if err_all.size else None,
+        "cd_rel_err_p90_all_converged": float(np.percentile(err_all, 90)) if err_all.size else None,
+        "solver_s_for_test": round(wall_solver, 3), "network_s_for_test": round(wall_net, 5),
+        "speedup_trusted": round(wall_solver / max(wall_net, 1e-9), 1),
+    }
+    return (summary, model) if return_model else summary
