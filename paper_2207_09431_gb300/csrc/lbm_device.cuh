@@ -61,7 +61,7 @@ __device__ __forceinline__ void mixture_weights(float C1, float C2, float C3, fl
   c[0] = fminf(fmaxf(C1, 0.0f), 1.0f);
   c[1] = fminf(fmaxf(C2, 0.0f), 1.0f);
   c[2] = fminf(fmaxf(C3, 0.0f), 1.0f);
-  float inv = 1.0f / (c[0] + c[1] + c[2]);
+  float inv = __fdividef(1.0f, c[0] + c[1] + c[2]);
   c[0] *= inv;
   c[1] *= inv;
   c[2] *= inv;
@@ -103,6 +103,19 @@ __device__ __forceinline__ float tau_powerlaw(const DevParams &P, float gd, floa
     t = P.n1 < 0.0f ? __int_as_float(0x7f800000) : (P.n1 > 0.0f ? 0.0f : P.k3 * irho);
   }
   t = (t <= P.tau_max) ? t : P.tau_max;  // also maps +inf to tau_max
+  return fmaxf(t, P.tau_min);
+}
+
+// The same from the squared strain rate gd2 = gd^2 (no square root):
+// gd^(n-1) = gd2^((n-1)/2).
+__device__ __forceinline__ float tau_powerlaw_sq(const DevParams &P, float gd2, float irho) {
+  float t;
+  if (gd2 > 0.0f) {
+    t = P.k3 * exp2f(P.n1h * __log2f(gd2)) * irho;
+  } else {
+    t = P.n1 < 0.0f ? __int_as_float(0x7f800000) : (P.n1 > 0.0f ? 0.0f : P.k3 * irho);
+  }
+  t = (t <= P.tau_max) ? t : P.tau_max;
   return fmaxf(t, P.tau_min);
 }
 

@@ -19,6 +19,7 @@ struct DevParams {
   float grad_coef[3];  // (3/4) xi Sigma_i (Eq. 5)
   float d0_sig[3];     // D0 / Sigma_i (Eq. 6)
   float n1, k3;        // n - 1 and k / cs^2 (Eq. 31-32)
+  float n1h;           // (n - 1) / 2
   long long plane;  // floats per plane (ny * pitch)
 };
 

@@ -173,8 +173,8 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
       c.gCx[i] = s.gCx[i][c2];
       c.gCy[i] = s.gCy[i][c2];
     }
-    float hs[NH][9], sv[NH], tn, gd;
-    node_collide<NH>(P, c, pn, rn, cn, mun, g, B.tau_in[k], hs, sv, tn, gd);
+    float hs[NH][9], sv[NH], tn, gd2;
+    node_collide<NH>(P, c, pn, rn, cn, mun, g, B.tau_in[k], hs, sv, tn, gd2);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       s.g[a][c2] = g[a];
@@ -184,7 +184,7 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
 #pragma unroll
     for (int i = 0; i < NH; ++i) s.sv[i][q] = sv[i];
     if (lx >= 0 && lx < TX && ly >= 0 && ly < TY && x0 + lx < nx && gy < ny)
-      store_diagnostics<NH>(B, plane, k, tn, gd, sv, c);
+      store_diagnostics<NH>(B, plane, k, tn, gd2, sv, c);
   }
   __syncthreads();
 

@@ -133,6 +133,7 @@ inline lbm::DevParams dev_params(const lbm_params &p) {
   }
   d.mu_pre = (float)(4.0 * (3.0 / (1.0 / S1 + 1.0 / S2 + 1.0 / S3)) / p.xi);
   d.n1 = (float)(p.pl_n - 1.0);
+  d.n1h = (float)(0.5 * (p.pl_n - 1.0));
   d.k3 = (float)(3.0 * p.pl_k);
   d.gravity = (float)p.gravity;
   d.force_x = (float)p.force_x;

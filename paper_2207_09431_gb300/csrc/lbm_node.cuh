@@ -67,7 +67,7 @@ __device__ __forceinline__ void node_fields(const DevParams &P, const float (&g)
     ry += wt(a) * ey(a) * rn[a];
   }
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
+  for (int j = 0; j < 2; ++j) {
     float sx = 0.f, sy = 0.f, lp = 0.f;
 #pragma unroll
     for (int a = 1; a < 9; ++a) {
@@ -80,13 +80,18 @@ __device__ __forceinline__ void node_fields(const DevParams &P, const float (&g)
     f.gCy[j] = 3.0f * sy;
     lap[j] = 6.0f * lp;
   }
+  // C_3 = 1 - C_1 - C_2 (Eq. 1): its stencils are minus the sum of the others'
+  C[2] = cc[2][0];
+  f.gCx[2] = -(f.gCx[0] + f.gCx[1]);
+  f.gCy[2] = -(f.gCy[0] + f.gCy[1]);
+  lap[2] = -(lap[0] + lap[1]);
   rx *= 3.0f;
   ry *= 3.0f;
   chem_potentials(P, C, lap, f.mu);
   const float Fsx = f.mu[0] * f.gCx[0] + f.mu[1] * f.gCx[1] + f.mu[2] * f.gCx[2];
   const float Fsy = f.mu[0] * f.gCy[0] + f.mu[1] * f.gCy[1] + f.mu[2] * f.gCy[2];
   const float rho = rn[0];
-  const float irho = 1.0f / rho;
+  const float irho = __fdividef(1.0f, rho);
   f.ux = (3.0f * mx + 0.5f * (Fsx + P.force_x)) * irho;
   f.uy = (3.0f * my + 0.5f * (Fsy - rho * P.gravity)) * irho;
   f.p = m0 + 0.5f * kCs2 * (f.ux * rx + f.uy * ry);
@@ -107,9 +112,9 @@ template <int NH>
 __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCenter &c, const float (&pn)[9],
                                              const float (&rn)[9], const float (&cn)[NH][9],
                                              const float (&mun)[NH][9], float (&g)[9], float tau_prev,
-                                             float (&hs)[NH][9], float (&sv)[NH], float &tn, float &gd) {
+                                             float (&hs)[NH][9], float (&sv)[NH], float &tn, float &gd2) {
   const float ux = c.ux, uy = c.uy, p = c.p, rho = c.rho;
-  const float irho = 1.0f / rho;
+  const float irho = __fdividef(1.0f, rho);
   float px = 0.f, py = 0.f, mgx[NH], mgy[NH], mlap[NH];
 #pragma unroll
   for (int i = 0; i < NH; ++i) mgx[i] = mgy[i] = mlap[i] = 0.f;
@@ -151,6 +156,26 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
   const float udp = ux * px + uy * py;
   const float uu = ux * ux + uy * uy;
   const float rcs2 = rho * kCs2;
+  // central directional derivatives along e_a (x + e_a and x - e_a); those
+  // of opposite directions are negatives of each other
+  float drv[9], dpv[9], dCv[NH][9];
+  drv[0] = dpv[0] = 0.f;
+#pragma unroll
+  for (int i = 0; i < NH; ++i) dCv[i][0] = 0.f;
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    if (a == 1 || a == 2 || a == 5 || a == 6) {
+      drv[a] = 0.5f * (rn[a] - rn[opp(a)]);
+      dpv[a] = 0.5f * (pn[a] - pn[opp(a)]);
+      drv[opp(a)] = -drv[a];
+      dpv[opp(a)] = -dpv[a];
+#pragma unroll
+      for (int i = 0; i < NH; ++i) {
+        dCv[i][a] = 0.5f * (cn[i][a] - cn[i][opp(a)]);
+        dCv[i][opp(a)] = -dCv[i][a];
+      }
+    }
+  }
   // equilibria and forcing of every direction, h*, momentum flux of g - g^eq
   float eqf[9];
   float Pxx = 0.f, Pyy = 0.f, Pxy = 0.f;
@@ -159,14 +184,13 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
     const float exa = (float)ex(a), eya = (float)ey(a), w = wt(a);
     const float eu = exa * ux + eya * uy;
     const float G = w * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-    // central directional derivatives along e_a (x + e_a and x - e_a)
-    const float dr = 0.5f * (rn[a] - rn[opp(a)]);
-    const float dp = 0.5f * (pn[a] - pn[opp(a)]);
+    const float dr = drv[a];
+    const float dp = dpv[a];
     float dC[NH];
     float eFs = -udFs;
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
-      dC[i] = 0.5f * (cn[i][a] - cn[i][opp(a)]);
+      dC[i] = dCv[i][a];
       eFs += c.dmu[i] * dC[i];
     }
     const float eFb = exa * P.force_x + eya * Fby - udFb;
@@ -186,13 +210,14 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
     }
   }
   // (1/cs^2) (2 tau / (2 tau + 1)) / (2 tau rho cs^2) = 9 / ((2 tau + 1) rho)
-  const float fac = 9.0f * irho / (2.0f * tau_prev + 1.0f);
+  const float fac = __fdividef(9.0f * irho, 2.0f * tau_prev + 1.0f);
   const float Dxx = -fac * Pxx, Dyy = -fac * Pyy, Dxy = -fac * Pxy;
-  gd = sqrtf(2.0f * (Dxx * Dxx + Dyy * Dyy + 2.0f * Dxy * Dxy));
+  // squared strain rate 2 D:D; the power law takes it without a square root
+  gd2 = 2.0f * (Dxx * Dxx + Dyy * Dyy + 2.0f * Dxy * Dxy);
   const float C3 = 1.0f - Cc[0] - (NH == 2 ? Cc[NH - 1] : 0.f);
-  const float tau1 = P.powerlaw ? tau_powerlaw(P, gd, irho) : P.tau[0];
+  const float tau1 = P.powerlaw ? tau_powerlaw_sq(P, gd2, irho) : P.tau[0];
   tn = tau_mix(P, Cc[0], NH == 2 ? Cc[NH - 1] : 0.f, C3, tau1);
-  const float om = 1.0f / (tn + 0.5f);
+  const float om = __fdividef(1.0f, tn + 0.5f);
 #pragma unroll
   for (int a = 0; a < 9; ++a) g[a] = (1.0f - om) * g[a] + eqf[a];
 }
@@ -257,12 +282,13 @@ __device__ __forceinline__ void load_populations(const DevParams &P, const Fused
   }
 }
 
-// New tau of an owned node, optional diagnostics, and the finiteness check.
+// New tau of an owned node, optional diagnostics (strain rate from its square
+// gd2), and the finiteness check.
 template <int NH>
 __device__ __forceinline__ void store_diagnostics(const FusedBuffers &B, long long plane, long long k, float tn,
-                                                  float gd, const float (&sv)[NH], const NodeCenter &c) {
+                                                  float gd2, const float (&sv)[NH], const NodeCenter &c) {
   B.tau_out[k] = tn;
-  if (B.shear) B.shear[k] = gd;
+  if (B.shear) B.shear[k] = sqrtf(gd2);
   if (B.SV) {
 #pragma unroll
     for (int i = 0; i < NH; ++i) B.SV[(long long)i * plane + k] = sv[i];

@@ -64,13 +64,14 @@ __device__ __forceinline__ int slot(int r, int base) {
   return (int)((unsigned)(r - base) % (unsigned)D);
 }
 
-template <int TX, int RS, int NH, int FORM, int NT, int MINB>
+template <int TX, int RS, int NH, int FORM, int PER, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffers B, int seg_len) {
   using S = PipeSmem<TX, RS, NH>;
   static_assert(NT >= RS * S::W3, "one item of every stage per thread");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S &s = *reinterpret_cast<S *>(smem_raw);
-  const int nx = P.nx, ny = P.ny, per = P.periodic_y, pitch = P.pitch;
+  constexpr int per = PER;
+  const int nx = P.nx, ny = P.ny, pitch = P.pitch;
   const long long plane = P.plane;
   const int x0 = blockIdx.x * TX;
   const int ys = blockIdx.y * seg_len;
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffe
   const int base = j0;  // ring rows are counted from here (all rows used are >= base)
 
   for (int j = j0; j < ye; j += RS) {
-    // ---- issue this step's global loads
+    // ---- issue this step's global loads; they are used after stage 3 and
+    // the collision
     const int r0 = j + 3 * RS + 3 + d0;
     const int r1 = j + 2 * RS + 2 + d1;
     const int r2 = j + RS + 1 + d2;
@@ -168,8 +170,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffe
         nc.gCx[q] = s.gCx[q][sa][c2];
         nc.gCy[q] = s.gCy[q][sa][c2];
       }
-      float hs[NH][9], sv[NH], tn, gd;
-      node_collide<NH>(P, nc, pn, rn, cn, mun, g2, tprev, hs, sv, tn, gd);
+      float hs[NH][9], sv[NH], tn, gd2;
+      node_collide<NH>(P, nc, pn, rn, cn, mun, g2, tprev, hs, sv, tn, gd2);
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         s.gs[a][sb][c2] = g2[a];
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffe
       for (int q = 0; q < NH; ++q) s.sv[q][sb][c2] = sv[q];
       s.uxb[sb][c2] = nc.ux;
       s.uyb[sb][c2] = nc.uy;
-      if (own2 && r2 >= ys && r2 < ye) store_diagnostics<NH>(B, plane, k2, tn, gd, sv, nc);
+      if (own2 && r2 >= ys && r2 < ye) store_diagnostics<NH>(B, plane, k2, tn, gd2, sv, nc);
     }
 
     // ---- stage 1: fields of row r1 (2-ring column c1)
@@ -248,21 +250,21 @@ int choose_segment(int ny, int strips, int resident, int rs) {
   return best_len;
 }
 
-template <int TX, int RS, int NH, int FORM, int NT, int MINB>
-cudaError_t launch_sweep_t(const DevParams &P, const FusedBuffers &B, cudaStream_t st) {
+template <int TX, int RS, int NH, int FORM, int PER, int NT, int MINB>
+cudaError_t launch_sweep_per(const DevParams &P, const FusedBuffers &B, cudaStream_t st) {
   const size_t smem = sizeof(PipeSmem<TX, RS, NH>);
   static bool configured = false;
   static int resident_per_sm = 0, sms = 0;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_step_sweep<TX, RS, NH, FORM, NT, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(k_step_sweep<TX, RS, NH, FORM, PER, NT, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident_per_sm, k_step_sweep<TX, RS, NH, FORM, NT, MINB>,
-                                                        NT, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident_per_sm,
+                                                        k_step_sweep<TX, RS, NH, FORM, PER, NT, MINB>, NT, smem);
     if (e != cudaSuccess) return e;
     if (resident_per_sm < 1) return cudaErrorInvalidConfiguration;
     configured = true;
@@ -270,8 +272,16 @@ cudaError_t launch_sweep_t(const DevParams &P, const FusedBuffers &B, cudaStream
   const int strips = (P.nx + TX - 1) / TX;
   const int len = choose_segment(P.ny, strips, resident_per_sm * sms, RS);
   const dim3 grd(strips, (P.ny + len - 1) / len);
-  k_step_sweep<TX, RS, NH, FORM, NT, MINB><<<grd, NT, smem, st>>>(P, B, len);
+  k_step_sweep<TX, RS, NH, FORM, PER, NT, MINB><<<grd, NT, smem, st>>>(P, B, len);
   return cudaGetLastError();
+}
+
+// Walls and periodic y are separate instantiations: the wall checks of every
+// stage vanish from the periodic kernel and vice versa.
+template <int TX, int RS, int NH, int FORM, int NT, int MINB>
+cudaError_t launch_sweep_t(const DevParams &P, const FusedBuffers &B, cudaStream_t st) {
+  return P.periodic_y ? launch_sweep_per<TX, RS, NH, FORM, 1, NT, MINB>(P, B, st)
+                      : launch_sweep_per<TX, RS, NH, FORM, 0, NT, MINB>(P, B, st);
 }
 
 }  // namespace
