@@ -95,24 +95,117 @@ __global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffe
   const int j0 = ys - 3 * RS - RS * ((6 + RS - 1) / RS);
   const int base = j0;  // ring rows are counted from here (all rows used are >= base)
 
+  // Global loads run one pipeline step ahead: the values a step consumes were
+  // requested during the previous step, so their latency overlaps a whole
+  // step of shared-memory work.  A thread's stage items move up RS rows per
+  // step, so the next step's items are this step's plus RS.
+  constexpr int NS0 = FORM == 0 ? 9 * NH : NH;
+  float nh[NS0];            // state values of the next stage-0 item
+  float ng[9];              // g of the next stage-1 item (FP32 forms)
+  __half ngh[9];            // ... (FP16 form: deviations and reference)
+  float nP = 0.f, nt = 0.f; // previous tau of the next stage-2 item
+  auto item_rows = [&](int j, int &r0, int &r1, int &r2, bool &a0, bool &a1, bool &a2) {
+    r0 = j + 3 * RS + 3 + d0;
+    r1 = j + 2 * RS + 2 + d1;
+    r2 = j + RS + 1 + d2;
+    a0 = v0 && r0 >= ys - 3 && r0 < ye + 3;
+    a1 = v1 && r1 >= ys - 2 && r1 < ye + 2 && (per || (r1 >= 0 && r1 < ny));
+    a2 = v2 && r2 >= ys - 1 && r2 < ye + 1 && (per || (r2 >= 0 && r2 < ny));
+  };
+  auto issue = [&](int j) {
+    int r0, r1, r2;
+    bool a0, a1, a2;
+    item_rows(j, r0, r1, r2, a0, a1, a2);
+    if (a0) {
+      const long long k0 = (long long)row_read(r0, ny, per) * pitch + x0c;
+#pragma unroll
+      for (int q = 0; q < NS0; ++q) nh[q] = B.h_in[(long long)q * plane + k0];
+    }
+    if (a1) {
+      const long long k1 = (long long)(per ? wrap_periodic(r1, ny) : r1) * pitch + x1c;
+      if constexpr (FORM == 2) {
+        const __half *gh = reinterpret_cast<const __half *>(B.g_in);
+        nP = B.g_in[(9 * plane) / 2 + k1];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) ngh[a] = gh[(long long)a * plane + k1];
+      } else {
+#pragma unroll
+        for (int a = 0; a < 9; ++a) ng[a] = B.g_in[(long long)a * plane + k1];
+      }
+    }
+    if (a2) nt = B.tau_in[(long long)(per ? wrap_periodic(r2, ny) : r2) * pitch + x2c];
+  };
+  issue(j0);
+
   for (int j = j0; j < ye; j += RS) {
-    // ---- issue this step's global loads; they are used after stage 3 and
-    // the collision
-    const int r0 = j + 3 * RS + 3 + d0;
-    const int r1 = j + 2 * RS + 2 + d1;
-    const int r2 = j + RS + 1 + d2;
+    int r0, r1, r2;
+    bool a0, a1, a2;
+    item_rows(j, r0, r1, r2, a0, a1, a2);
     const int r3 = j + d3;
-    const bool a0 = v0 && r0 >= ys - 3 && r0 < ye + 3;
-    const bool a1 = v1 && r1 >= ys - 2 && r1 < ye + 2 && (per || (r1 >= 0 && r1 < ny));
-    const bool a2 = v2 && r2 >= ys - 1 && r2 < ye + 1 && (per || (r2 >= 0 && r2 < ny));
     const bool a3 = out3 && r3 >= ys && r3 < ye;
-    float cst[NH];
-    if (a0) load_order_parameters<NH, FORM>(B, plane, (long long)row_read(r0, ny, per) * pitch + x0c, cst);
-    float gv[9];
-    const long long k1 = (long long)(per ? wrap_periodic(r1, ny) : r1) * pitch + x1c;
-    if (a1) load_populations<FORM>(P, B, plane, k1, gv);
     const long long k2 = (long long)(per ? wrap_periodic(r2, ny) : r2) * pitch + x2c;
-    const float tprev = a2 ? B.tau_in[k2] : 0.f;
+
+    // ---- stage 0: C and rho of row r0 (3-ring column c0), from the loads of
+    // the previous step
+    if (a0) {
+      float cst[NH];
+#pragma unroll
+      for (int q = 0; q < NH; ++q) {
+        if constexpr (FORM == 0) {
+          float acc = 0.f;
+#pragma unroll
+          for (int a = 0; a < 9; ++a) acc += nh[q * 9 + a];
+          cst[q] = acc;
+        } else {
+          cst[q] = nh[q];
+        }
+      }
+      const int sc = slot<S::D3>(r0, base);
+#pragma unroll
+      for (int q = 0; q < NH; ++q) s.C[q][sc][c0] = cst[q];
+      s.rho[sc][c0] = node_rho<NH>(P, cst);
+    }
+
+    // ---- stage 1: fields of row r1 (2-ring column c1)
+    if (a1) {
+      float gv[9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        if constexpr (FORM == 2) gv[a] = g16_decode(nP, ngh[a], a, P.g16_inv_scale);
+        else gv[a] = ng[a];
+      }
+      float cn[NH][9], rn[9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        const int sc = slot<S::D3>(r1 + ey(a), base);
+#pragma unroll
+        for (int q = 0; q < NH; ++q) cn[q][a] = s.C[q][sc][c1 + 1 + ex(a)];
+        rn[a] = s.rho[sc][c1 + 1 + ex(a)];
+      }
+      NodeFields f;
+      node_fields<NH>(P, gv, cn, rn, f);
+      const int sm = slot<S::D2>(r1, base);
+#pragma unroll
+      for (int q = 0; q < NH; ++q) s.mu[q][sm][c1] = f.mu[q];
+      s.p[sm][c1] = f.p;
+      if (c1 >= 1 && c1 <= TX + 2) {
+        const int sa = slot<S::DA>(r1, base), cc = c1 - 1;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) s.g[a][sa][cc] = gv[a];
+#pragma unroll
+        for (int q = 0; q < NH; ++q) {
+          s.dmu[q][sa][cc] = f.mu[q] - f.mu[2];
+          s.gCx[q][sa][cc] = f.gCx[q];
+          s.gCy[q][sa][cc] = f.gCy[q];
+        }
+        s.ux[sa][cc] = f.ux;
+        s.uy[sa][cc] = f.uy;
+        s.grx[sa][cc] = f.rx;
+        s.gry[sa][cc] = f.ry;
+      }
+    }
+    const float tprev = nt;
+    issue(j + RS);  // the next step's loads
 
     // ---- stage 3: arriving populations of output row r3
     if (a3) {
@@ -185,46 +278,6 @@ __global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffe
       if (own2 && r2 >= ys && r2 < ye) store_diagnostics<NH>(B, plane, k2, tn, gd2, sv, nc);
     }
 
-    // ---- stage 1: fields of row r1 (2-ring column c1)
-    if (a1) {
-      float cn[NH][9], rn[9];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        const int sc = slot<S::D3>(r1 + ey(a), base);
-#pragma unroll
-        for (int q = 0; q < NH; ++q) cn[q][a] = s.C[q][sc][c1 + 1 + ex(a)];
-        rn[a] = s.rho[sc][c1 + 1 + ex(a)];
-      }
-      NodeFields f;
-      node_fields<NH>(P, gv, cn, rn, f);
-      const int sm = slot<S::D2>(r1, base);
-#pragma unroll
-      for (int q = 0; q < NH; ++q) s.mu[q][sm][c1] = f.mu[q];
-      s.p[sm][c1] = f.p;
-      if (c1 >= 1 && c1 <= TX + 2) {
-        const int sa = slot<S::DA>(r1, base), cc = c1 - 1;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) s.g[a][sa][cc] = gv[a];
-#pragma unroll
-        for (int q = 0; q < NH; ++q) {
-          s.dmu[q][sa][cc] = f.mu[q] - f.mu[2];
-          s.gCx[q][sa][cc] = f.gCx[q];
-          s.gCy[q][sa][cc] = f.gCy[q];
-        }
-        s.ux[sa][cc] = f.ux;
-        s.uy[sa][cc] = f.uy;
-        s.grx[sa][cc] = f.rx;
-        s.gry[sa][cc] = f.ry;
-      }
-    }
-
-    // ---- stage 0: C and rho of row r0 (3-ring column c0)
-    if (a0) {
-      const int sc = slot<S::D3>(r0, base);
-#pragma unroll
-      for (int q = 0; q < NH; ++q) s.C[q][sc][c0] = cst[q];
-      s.rho[sc][c0] = node_rho<NH>(P, cst);
-    }
     __syncthreads();
   }
 }
@@ -288,10 +341,10 @@ cudaError_t launch_sweep_t(const DevParams &P, const FusedBuffers &B, cudaStream
 
 // Launch configurations of the row sweep: strip width x rows per pipeline
 // step / threads / minimum resident CTAs per SM.
-int sweep_variant_count(const DevParams &P) { return P.nh == 1 ? 5 : 3; }
+int sweep_variant_count(const DevParams &P) { return P.nh == 1 ? 6 : 3; }
 
 const char *sweep_variant_name(const DevParams &P, int v) {
-  static const char *n1[5] = {"64x2/160/3", "32x4/160/3", "128x1/160/2", "64x4/288/2", "64x1/96/5"};
+  static const char *n1[6] = {"64x2/160/3", "32x4/160/3", "128x1/160/2", "64x4/288/2", "64x1/96/5", "32x8/320/2"};
   static const char *n2[3] = {"64x2/160/2", "32x4/160/2", "64x1/96/4"};
   if (v < 0 || v >= sweep_variant_count(P)) v = 0;
   return P.nh == 1 ? n1[v] : n2[v];
@@ -305,6 +358,7 @@ static cudaError_t sweep_dispatch(int v, const DevParams &P, const FusedBuffers 
       case 2: return launch_sweep_t<128, 1, NH, FORM, 160, 2>(P, B, s);
       case 3: return launch_sweep_t<64, 4, NH, FORM, 288, 2>(P, B, s);
       case 4: return launch_sweep_t<64, 1, NH, FORM, 96, 5>(P, B, s);
+      case 5: return launch_sweep_t<32, 8, NH, FORM, 320, 2>(P, B, s);
       default: return launch_sweep_t<64, 2, NH, FORM, 160, 3>(P, B, s);
     }
   } else {
