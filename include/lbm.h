@@ -78,6 +78,18 @@ typedef struct {
                           the same C, g, tau up to FP32 summation order; form 1 moves
                           88 instead of 152 bytes per node-step (2 components).  Needs
                           fd_scheme 0; LBM_FIELD_H is then unavailable. */
+  int open_x;          /* 0: periodic in x.  1: velocity inlet at x = 0 and convective
+                          outlet at x = nx - 1 (the channel of Sec. 3.2): stencils mirror
+                          the edge columns; g entering at x = 0 is the equilibrium at
+                          (u_in, 0) plus the non-equilibrium part of column 0, h entering
+                          there is c_in Gamma(u_in); populations entering at x = nx - 1
+                          follow f(t+1) = (f(t) + U f_(nx-2)(t+1)) / (1 + U), U the node's
+                          x velocity clamped to [0, 1], then share the shift that sets the
+                          node's pressure sum_a g_a to 0.  Needs nx >= 4, the population
+                          state (collapse_h 0, storage 0); runs on the multi-pass kernels;
+                          not in batches. */
+  double u_in;         /* inlet velocity (open_x) */
+  double c_in[2];      /* inflow composition C_1, C_2 (open_x) */
 } lbm_params;
 
 /* A disc of component `comp` (Eq. 42 profile). */

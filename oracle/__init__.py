@@ -67,6 +67,7 @@ class _Params(ctypes.Structure):
         ("mobility", ctypes.c_int),
         ("gravity", ctypes.c_double), ("force_x", ctypes.c_double),
         ("fd_scheme", ctypes.c_int),
+        ("open_x", ctypes.c_int), ("u_in", ctypes.c_double), ("c_in", ctypes.c_double * 2),
     ]
 
 
@@ -98,7 +99,8 @@ FIELD_IDS = {"C1": 0, "C2": 1, "C3": 2, "rho": 3, "p": 4, "ux": 5, "uy": 6, "tau
 DEFAULTS = dict(periodic_y=0, rho=(1.0, 1.0, 1.0), tau=(0.5, 0.5, 0.5), powerlaw=0,
                 pl_n=1.0, pl_k=1.0 / 6.0, tau_min=0.01, tau_max=3.0, sigma12=1e-3,
                 sigma13=1e-3, sigma23=1e-3, Lambda=0.0, xi=4.0, D0=4.0 / 300.0,
-                mobility=0, gravity=0.0, force_x=0.0, fd_scheme=0, gas_comp=3)
+                mobility=0, gravity=0.0, force_x=0.0, fd_scheme=0, gas_comp=3,
+                open_x=0, u_in=0.0, c_in=(1.0, 0.0))
 
 
 def _dptr(a):
@@ -120,6 +122,8 @@ class Oracle:
             if name in ("rho", "tau"):
                 arr = (ctypes.c_double * 3)(*[float(x) for x in v])
                 setattr(pr, name, arr)
+            elif name == "c_in":
+                setattr(pr, name, (ctypes.c_double * 2)(*[float(x) for x in v]))
             elif ctype is ctypes.c_int:
                 setattr(pr, name, int(v))
             else:

@@ -51,6 +51,21 @@
  *       barred populations; Eq. 29 already converts them to f - f^eq with
  *       2 tau / (2 tau + 1).  Applying both under-reads the strain rate by
  *       tau / (tau + 1/2), so D = -Pi / (2 tau rho cs^2) with Pi from Eq. 29.
+ *   R27 open x boundaries (the channel of Sec. 3.2 names a velocity inlet and a
+ *       convective outlet without their discrete form): stencils read ghost
+ *       columns that mirror the fluid columns; the populations entering at
+ *       x = 0 come from a ghost column x = -1 whose post-collision g is the
+ *       equilibrium at the inlet velocity plus the non-equilibrium part of the
+ *       post-collision g of column 0 (non-equilibrium extrapolation,
+ *       equilibria w p + rho cs^2 (Gamma - w) without forcing), and whose h is
+ *       the equilibrium C_in Gamma at the inlet velocity for the given inflow
+ *       composition C_in; the populations entering at x = nx - 1 follow the
+ *       convective condition f(t+1) = (f(t) + U f_(nx-2)(t+1)) / (1 + U)
+ *       with U the node's x velocity clamped to [0, 1], and then share, by
+ *       weight, the shift that brings the node's zeroth moment of g to zero
+ *       (a pressure reference: without it the inflow and the extrapolated
+ *       outflow do not balance and the pressure level drifts).  Wall rows keep
+ *       their bounce-back.
  */
 #include <math.h>
 #include <stdint.h>
@@ -78,6 +93,9 @@ typedef struct {
   double gravity;  /* F_b = -rho g j (Eq. 12) */
   double force_x;  /* uniform body-force density along x (drives the channel tests of Sec. 3.2-3.3) */
   int fd_scheme;   /* 0 central, 1 mixed directional differences */
+  int open_x;      /* 0 periodic in x; 1 velocity inlet at x = 0, convective outlet at x = nx - 1 (R27) */
+  double u_in;     /* inlet velocity along x */
+  double c_in[2];  /* composition C_1, C_2 of the inflow */
 } orc_params;
 
 /* D2Q9 (Eq. 10, 11): 0 rest, 1-4 = E N W S, 5-8 = NE NW SW SE. */
@@ -107,17 +125,27 @@ typedef struct {
   real *drho, *dC[3], *dp, *Phig, *Phih[2], *geqb, *heqb[2];
   /* node index of x + e_a and x + 2 e_a under the ghost rule of reading R10 */
   size_t *nb1, *nb2;
+  /* populations of the outlet column before streaming (open x, R27) */
+  real *gold, *hold;
 } orc_state;
 
 /* ---------------------------------------------------------------- helpers */
 
 static size_t idx(const orc_state *s, int x, int y) { return (size_t)y * s->p.nx + x; }
 
-/* Node index holding the value seen at (x, y): periodic x, and either periodic
- * y or the mirror ghost rows of reading R10. */
+/* Node index holding the value seen at (x, y): periodic x (or mirror ghost
+ * columns for open x, R27), and either periodic y or the mirror ghost rows of
+ * reading R10. */
 static size_t wrap_index(const orc_state *s, int x, int y) {
   int nx = s->p.nx, ny = s->p.ny;
-  x = ((x % nx) + nx) % nx;
+  if (s->p.open_x) {
+    while (x < 0 || x >= nx) {
+      if (x < 0) x = -1 - x;
+      if (x >= nx) x = 2 * nx - 1 - x;
+    }
+  } else {
+    x = ((x % nx) + nx) % nx;
+  }
   if (s->p.periodic_y) {
     y = ((y % ny) + ny) % ny;
   } else {
@@ -340,6 +368,7 @@ orc_state *orc_create(const orc_params *prm) {
   if (!prm || prm->nx < 1 || prm->ny < 2 || (prm->ncomp != 2 && prm->ncomp != 3)) return NULL;
   if (prm->fd_scheme != 0 && prm->fd_scheme != 1) return NULL;
   if (!prm->periodic_y && prm->fd_scheme == 1 && prm->ny < 3) return NULL;
+  if (prm->open_x && prm->nx < 4) return NULL;
   orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
   if (!s) return NULL;
   s->p = *prm;
@@ -392,6 +421,8 @@ orc_state *orc_create(const orc_params *prm) {
   for (int j = 0; j < 3; ++j) s->dC[j] = calloc(9 * n, sizeof(real));
   s->Phig = calloc(9 * n, sizeof(real));
   s->geqb = calloc(9 * n, sizeof(real));
+  s->gold = calloc(9 * (size_t)prm->ny, sizeof(real));
+  s->hold = calloc((size_t)s->nh * 9 * prm->ny, sizeof(real));
   return s;
 }
 
@@ -407,6 +438,7 @@ void orc_destroy(orc_state *s) {
   }
   for (int i = 0; i < 2; ++i) { free(s->S[i]); free(s->V[i]); free(s->Phih[i]); free(s->heqb[i]); }
   free(s->drho); free(s->dp); free(s->Phig); free(s->geqb); free(s->nb1); free(s->nb2);
+  free(s->gold); free(s->hold);
   for (int j = 0; j < 3; ++j) free(s->dC[j]);
   free(s);
 }
@@ -520,6 +552,63 @@ int orc_init_bubbles(orc_state *s, const double *bubbles, int nb, unsigned long 
   return rc;
 }
 
+/* Populations entering through the open x boundaries (reading R27), after the
+ * periodic pull of the streaming loop has written placeholders there.  Wall
+ * rows keep the bounce-back of that loop. */
+static real geq_plain(int a, real p, real rho, real ux, real uy) {
+  return W[a] * p + rho * CS2 * (Gamma(a, ux, uy) - W[a]);
+}
+
+static void open_boundaries(orc_state *s) {
+  const size_t n = s->n;
+  const int nx = s->p.nx, ny = s->p.ny;
+  const real uin = s->p.u_in;
+  for (int y = 0; y < ny; ++y) {
+    /* inlet: directions with e_x = +1 leave the ghost column x = -1 */
+    size_t k = idx(s, 0, y);
+    for (int a = 0; a < 9; ++a) {
+      if (EX[a] != 1) continue;
+      int sy = y - EY[a];
+      if (!s->p.periodic_y && (sy < 0 || sy >= ny)) continue;
+      sy = ((sy % ny) + ny) % ny;
+      size_t k0 = idx(s, 0, sy);
+      real gpost0 = s->gpost[(size_t)a * n + k0];
+      s->g[(size_t)a * n + k] = geq_plain(a, s->pr[k0], s->rho[k0], uin, 0.0) +
+                                (gpost0 - geq_plain(a, s->pr[k0], s->rho[k0], s->ux[k0], s->uy[k0]));
+      real G = Gamma(a, s->ux[k], s->uy[k]);
+      for (int i = 0; i < s->nh; ++i)
+        s->h[((size_t)i * 9 + a) * n + k] = s->p.c_in[i] * Gamma(a, uin, 0.0) + 0.5 * (s->S[i][k] + s->V[i][k]) * G;
+    }
+    /* outlet: directions with e_x = -1 would leave the ghost column x = nx */
+    k = idx(s, nx - 1, y);
+    size_t kin = idx(s, nx - 2, y);
+    real U = s->ux[k];
+    U = U < 0.0 ? 0.0 : (U > 1.0 ? 1.0 : U);
+    real wsum = 0.0;
+    int set[9] = {0};
+    for (int a = 0; a < 9; ++a) {
+      if (EX[a] != -1) continue;
+      int sy = y - EY[a];
+      if (!s->p.periodic_y && (sy < 0 || sy >= ny)) continue;
+      set[a] = 1;
+      wsum += W[a];
+      s->g[(size_t)a * n + k] = (s->gold[(size_t)a * ny + y] + U * s->g[(size_t)a * n + kin]) / (1.0 + U);
+      for (int i = 0; i < s->nh; ++i) {
+        size_t ia = (size_t)i * 9 + a;
+        s->h[ia * n + k] = (s->hold[ia * ny + y] + U * s->h[ia * n + kin]) / (1.0 + U);
+      }
+    }
+    /* pressure anchor: the entering populations share, by weight, the shift
+     * that brings the node's zeroth moment of g to zero */
+    if (wsum > 0.0) {
+      real p0 = 0.0;
+      for (int a = 0; a < 9; ++a) p0 += s->g[(size_t)a * n + k];
+      for (int a = 0; a < 9; ++a)
+        if (set[a]) s->g[(size_t)a * n + k] -= p0 * W[a] / wsum;
+    }
+  }
+}
+
 /* One time step: Sec. 2.2-2.3 in the order moments -> mu -> gradients -> u, p
  * -> tau update -> collision of g and h -> streaming with bounce-back and the
  * destination-side terms of Eq. 18. */
@@ -584,6 +673,14 @@ static void one_step(orc_state *s) {
                         0.5 * (s->S[i][k] + s->V[i][k]) * G;
       }
     }
+  if (s->p.open_x)
+    for (int y = 0; y < ny; ++y)
+      for (int a = 0; a < 9; ++a) {
+        size_t k = idx(s, nx - 1, y);
+        s->gold[(size_t)a * ny + y] = s->g[(size_t)a * n + k];
+        for (int i = 0; i < s->nh; ++i)
+          s->hold[((size_t)i * 9 + a) * ny + y] = s->h[((size_t)i * 9 + a) * n + k];
+      }
   /* Streaming: population a arriving at y left y - e_a; across a wall it is
    * the population leaving y in the opposite direction (half-way bounce-back),
    * then the destination-side terms of Eq. 18 at the arrival node (R9). */
@@ -613,6 +710,7 @@ static void one_step(orc_state *s) {
               s->hpost[((size_t)i * 9 + aa) * n + src] + 0.5 * (s->S[i][k] + s->V[i][k]) * G;
       }
     }
+  if (s->p.open_x) open_boundaries(s);
   memcpy(s->tau, s->tau_new, n * sizeof(real));
   s->step += 1;
 }

@@ -102,7 +102,7 @@ size_t lbm_batch_required_bytes(const lbm_params *cases, int ncases) {
   size_t total = 0;
   for (int i = 0; i < ncases; ++i) {
     const size_t b = lbm_required_bytes(&cases[i]);
-    if (b == 0 || cases[i].storage != 0) return 0;  // batches hold FP32 states
+    if (b == 0 || cases[i].storage != 0 || cases[i].open_x) return 0;  // periodic FP32 states only
     total += align_up(b, kAlign);
   }
   total += batch_table_bytes(ncases) + batch_err_bytes(ncases);

@@ -8,6 +8,8 @@ struct DevParams {
   int nx, ny, pitch, ncomp, nh, periodic_y, powerlaw, mobility, fd_scheme;
   int collapse_h;  // 1: the state holds C_i instead of the populations h^i
   int g16;         // 1: g stored as FP16 deviations (with collapse_h)
+  int open_x;      // 1: velocity inlet at x = 0, convective outlet at x = nx - 1
+  float u_in, c_in[2];
   float g16_scale, g16_inv_scale;
   float rho[3], tau[3];
   float pl_n, pl_k, tau_min, tau_max;

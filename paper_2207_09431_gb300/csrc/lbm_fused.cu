@@ -420,6 +420,6 @@ cudaError_t launch_g16_decode(const DevParams &P, const float *g16, float *g32, 
   return cudaGetLastError();
 }
 
-bool fused_supported(const DevParams &P) { return P.fd_scheme == 0; }
+bool fused_supported(const DevParams &P) { return P.fd_scheme == 0 && !P.open_x; }
 
 }  // namespace lbm

@@ -63,6 +63,8 @@ inline const char *validate(const lbm_params *p) {
   if (p->fd_scheme != 0 && p->fd_scheme != 1) return "fd_scheme must be 0 or 1";
   if (p->storage != 0 && p->storage != 1) return "storage must be 0 (FP32) or 1 (FP16 g)";
   if (p->storage == 1 && !p->collapse_h) return "FP16 storage needs collapse_h 1";
+  if (p->open_x != 0 && p->open_x != 1) return "open_x must be 0 or 1";
+  if (p->open_x && (p->nx < 4 || p->collapse_h || p->storage)) return "open x needs nx >= 4 and the population state";
   if (p->mobility != 0 && p->mobility != 1) return "mobility must be 0 or 1";
   if (p->gas_comp != 2 && p->gas_comp != 3) return "gas_comp must be 2 or 3";
   if (p->ncomp == 2 && p->gas_comp != 3) return "with two components the gas is component 3";
@@ -94,6 +96,10 @@ inline lbm::DevParams dev_params(const lbm_params &p) {
   d.fd_scheme = p.fd_scheme;
   d.collapse_h = p.collapse_h;
   d.g16 = p.storage == 1 ? 1 : 0;
+  d.open_x = p.open_x;
+  d.u_in = (float)p.u_in;
+  d.c_in[0] = (float)p.c_in[0];
+  d.c_in[1] = (float)p.c_in[1];
   {
     // power-of-two scale: deviations of size rho_max stay far below the FP16
     // maximum (65504 / 2^14 = 4 rho_max) while those of size 1e-8 rho_max are

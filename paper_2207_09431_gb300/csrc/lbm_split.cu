@@ -30,8 +30,17 @@ __device__ __forceinline__ long long node_index(const DevParams &P, int x, int y
   return (long long)y * P.pitch + x;
 }
 
+// Column seen at x: periodic, or (open x) the mirror ghost columns beyond the
+// inlet and outlet, for offsets of at most two columns.
+__device__ __forceinline__ int column_of(const DevParams &P, int x) {
+  if (!P.open_x) return wrap_x(x, P.nx);
+  if (x < 0) x = -1 - x;
+  if (x >= P.nx) x = 2 * P.nx - 1 - x;
+  return x;
+}
+
 __device__ __forceinline__ long long shifted(const DevParams &P, int x, int y, int dx, int dy) {
-  return node_index(P, wrap_x(x + dx, P.nx), wrap_y(y + dy, P.ny, P.periodic_y));
+  return node_index(P, column_of(P, x + dx), wrap_y(y + dy, P.ny, P.periodic_y));
 }
 
 // Directional derivative e_a . grad X from samples X(x - e), X(x), X(x + e),
@@ -300,6 +309,8 @@ __global__ void k_collide(DevParams P, const float *__restrict__ g, const float 
     if (!P.periodic_y && (dy < 0 || dy >= P.ny)) {
       kd = k;
       da = opp(a);
+    } else if (P.open_x && (dx < 0 || dx >= P.nx)) {
+      continue;  // leaves through the inlet or outlet; k_open_x sets what enters
     } else {
       kd = node_index(P, wrap_x(dx, P.nx), P.periodic_y ? wrap_y(dy, P.ny, 1) : dy);
     }
@@ -309,6 +320,75 @@ __global__ void k_collide(DevParams P, const float *__restrict__ g, const float 
       const float ph = phi_h(n, i, a, G);
       const float hstar = n.C[i] * G + 0.5f * ph + 0.5f * sv[i] * G;
       h_out[((long long)i * 9 + da) * P.plane + kd] = hstar + 0.5f * SV[(long long)i * P.plane + kd] * Gd;
+    }
+  }
+}
+
+// Populations entering through the open x boundaries, after k_collide (one
+// thread per row).  Inlet (x = 0, e_x = +1): g from a ghost column x = -1 whose
+// post-collision g is the equilibrium w p + rho cs^2 (Gamma - w) at (u_in, 0)
+// plus the non-equilibrium part of column 0's post-collision g (which k_collide
+// stored at column 1), h the equilibrium c_in Gamma(u_in) plus the node's
+// destination-side term.  Outlet (x = nx - 1, e_x = -1): the convective
+// condition f(t+1) = (f(t) + U f_(nx-2)(t+1)) / (1 + U), U the node's x velocity
+// clamped to [0, 1], then the shift (shared by weight among the entering g)
+// that sets the node's pressure sum_a g_a to 0.  Wall rows keep bounce-back.
+__global__ void k_open_x(DevParams P, const float *__restrict__ g_old, const float *__restrict__ h_old,
+                         const float *__restrict__ Cf, const float *__restrict__ pf, const float *__restrict__ uxf,
+                         const float *__restrict__ uyf, const float *__restrict__ SV, float *__restrict__ g_out,
+                         float *__restrict__ h_out) {
+  const int y = blockIdx.x * blockDim.x + threadIdx.x;
+  if (y >= P.ny) return;
+  const long long pl = P.plane;
+  CReader cr{Cf, P.plane, P.nh};
+  // inlet
+  {
+    const long long k = node_index(P, 0, y), k1 = node_index(P, 1, y);
+    for (int a = 0; a < 9; ++a) {
+      if (ex(a) != 1) continue;
+      int sy = y - ey(a);
+      if (!P.periodic_y && (sy < 0 || sy >= P.ny)) continue;
+      sy = wrap_y(sy, P.ny, P.periodic_y);
+      const long long k0 = node_index(P, 0, sy);
+      float c[3];
+      cr.at(k0, c);
+      const float rho = rho_of(P, c[0], c[1], c[2]);
+      const float p = pf[k0];
+      const float w = wt(a);
+      const float eq_in = w * p + rho * kCs2 * (gamma_a(a, P.u_in, 0.0f) - w);
+      const float eq_0 = w * p + rho * kCs2 * (gamma_a(a, uxf[k0], uyf[k0]) - w);
+      g_out[(long long)a * pl + k] = eq_in + (g_out[(long long)a * pl + k1] - eq_0);
+      const float G = gamma_a(a, uxf[k], uyf[k]);
+      const float Gin = gamma_a(a, P.u_in, 0.0f);
+      for (int i = 0; i < P.nh; ++i)
+        h_out[((long long)i * 9 + a) * pl + k] = P.c_in[i] * Gin + 0.5f * SV[(long long)i * pl + k] * G;
+    }
+  }
+  // outlet
+  {
+    const long long k = node_index(P, P.nx - 1, y), kin = node_index(P, P.nx - 2, y);
+    const float U = fminf(fmaxf(uxf[k], 0.0f), 1.0f);
+    const float inv = 1.0f / (1.0f + U);
+    float wsum = 0.f;
+    bool set[9];
+    for (int a = 0; a < 9; ++a) {
+      set[a] = false;
+      if (ex(a) != -1) continue;
+      const int sy = y - ey(a);
+      if (!P.periodic_y && (sy < 0 || sy >= P.ny)) continue;
+      set[a] = true;
+      wsum += wt(a);
+      g_out[(long long)a * pl + k] = (g_old[(long long)a * pl + k] + U * g_out[(long long)a * pl + kin]) * inv;
+      for (int i = 0; i < P.nh; ++i) {
+        const long long ia = ((long long)i * 9 + a) * pl;
+        h_out[ia + k] = (h_old[ia + k] + U * h_out[ia + kin]) * inv;
+      }
+    }
+    if (wsum > 0.f) {
+      float p0 = 0.f;
+      for (int a = 0; a < 9; ++a) p0 += g_out[(long long)a * pl + k];
+      for (int a = 0; a < 9; ++a)
+        if (set[a]) g_out[(long long)a * pl + k] -= p0 * wt(a) / wsum;
     }
   }
 }
@@ -410,6 +490,8 @@ void launch_split_step(const DevParams &P, const StepBuffers &B, cudaStream_t s,
   k_sources<<<grd, blk, 0, s>>>(P, B.C, B.mu, B.SV);
   if (ev) cudaEventRecord(ev[3], s);
   k_collide<<<grd, blk, 0, s>>>(P, B.g_in, B.C, B.mu, B.p, B.ux, B.uy, B.tau_out, B.SV, B.g_out, B.h_out);
+  if (P.open_x)
+    k_open_x<<<(P.ny + 127) / 128, 128, 0, s>>>(P, B.g_in, B.h_in, B.C, B.p, B.ux, B.uy, B.SV, B.g_out, B.h_out);
   if (ev) cudaEventRecord(ev[4], s);
 }
 

@@ -215,6 +215,22 @@ def layered_channel_case(n, k, force, tau_outer=0.8, H=25, nx=2, xi=4.0, sigma=5
     return p, np.repeat(C1[None, :, None], nx, axis=2)
 
 
+def open_channel_case(n, ny=20, nx=40, u_in=0.04, tau_wall=0.8, tau_min=0.02, tau_max=20.0):
+    """Single-phase power-law channel of Sec. 3.2 between walls at y = -0.5 and
+    y = ny - 0.5, velocity inlet at x = 0 and convective outlet at x = nx - 1,
+    filled with component 1 (the power-law component; the paper fills it with
+    its component 3, the same fluid under another label).  The consistency k
+    gives tau = tau_wall at the wall shear rate of the fully developed profile
+    with mean velocity u_in.  Returns (params, C, ux) with the channel at rest
+    in pressure and moving at u_in."""
+    H = ny / 2.0
+    gw = u_in * (2 * n + 1) / n / H
+    k = (tau_wall / 3.0) / gw ** (n - 1.0)
+    p = dict(nx=nx, ny=ny, ncomp=2, periodic_y=0, rho=(1.0, 1.0, 1.0), tau=(tau_wall,) * 3, powerlaw=1,
+             pl_n=n, pl_k=k, tau_min=tau_min, tau_max=tau_max, open_x=1, u_in=u_in, c_in=(1.0, 0.0))
+    return p, np.ones((1, ny, nx)), np.full((ny, nx), u_in)
+
+
 ENSEMBLE_GRIDS = ((100, 200), (150, 300), (200, 400), (300, 600))
 
 

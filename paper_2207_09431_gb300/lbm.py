@@ -40,7 +40,8 @@ class lbm_params(ctypes.Structure):
         ("Lambda", ctypes.c_double), ("xi", ctypes.c_double), ("D0", ctypes.c_double),
         ("mobility", ctypes.c_int), ("gravity", ctypes.c_double), ("force_x", ctypes.c_double),
         ("fd_scheme", ctypes.c_int), ("storage", ctypes.c_int), ("gas_comp", ctypes.c_int),
-        ("collapse_h", ctypes.c_int),
+        ("collapse_h", ctypes.c_int), ("open_x", ctypes.c_int), ("u_in", ctypes.c_double),
+        ("c_in", ctypes.c_double * 2),
     ]
 
 
@@ -61,7 +62,7 @@ class lbm_obs(ctypes.Structure):
 DEFAULTS = dict(periodic_y=0, rho=(1.0, 1.0, 1.0), tau=(0.5, 0.5, 0.5), powerlaw=0, pl_n=1.0,
                 pl_k=1.0 / 6.0, tau_min=0.01, tau_max=3.0, sigma12=1e-3, sigma13=1e-3, sigma23=1e-3,
                 Lambda=0.0, xi=4.0, D0=4.0 / 300.0, mobility=0, gravity=0.0, force_x=0.0, fd_scheme=0,
-                storage=0, gas_comp=3, collapse_h=0)
+                storage=0, gas_comp=3, collapse_h=0, open_x=0, u_in=0.0, c_in=(1.0, 0.0))
 
 EXPORTED = ["lbm_version", "lbm_required_bytes", "lbm_create", "lbm_init_bubbles", "lbm_set_fields",
             "lbm_step", "lbm_observables", "lbm_get_field", "lbm_save", "lbm_load", "lbm_destroy",
@@ -148,6 +149,8 @@ def make_params(params: dict) -> lbm_params:
         v = full[name]
         if name in ("rho", "tau"):
             setattr(pr, name, (ctypes.c_double * 3)(*[float(x) for x in v]))
+        elif name == "c_in":
+            setattr(pr, name, (ctypes.c_double * 2)(*[float(x) for x in v]))
         elif ctype is ctypes.c_int:
             setattr(pr, name, int(v))
         else:

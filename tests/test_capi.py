@@ -57,6 +57,12 @@ def test_required_bytes_and_validation():
     assert lbm.lbm_required_bytes(q) == lbm.lbm_required_bytes(dict(q, storage=0)) > 0
     assert lbm.lbm_batch_required_bytes([q]) == 0
     assert lbm.lbm_batch_required_bytes([dict(q, storage=0)]) > 0
+    # open x boundaries: population state only, at least 4 columns, not batched
+    o = dict(p, open_x=1, u_in=0.02)
+    assert lbm.lbm_required_bytes(o) > 0
+    assert lbm.lbm_required_bytes(dict(o, collapse_h=1)) == 0
+    assert lbm.lbm_required_bytes(dict(o, nx=3)) == 0
+    assert lbm.lbm_batch_required_bytes([o]) == 0
 
 
 def test_postprocess_matches_oracle_formulas():

@@ -116,6 +116,46 @@ def test_layered_two_phase_channel_closed_form(n, tau_in):
     assert abs(abs(ycross) - 0.5 * H) < 0.05
 
 
+# ------------------------------------------------------------------ P1c
+@pytest.mark.parametrize("n,ny", [(0.5, 32), (1.0, 20), (1.5, 20)])
+def test_open_channel_inlet_outlet(n, ny):
+    """Sec. 3.2 in its own set-up: uniform inflow at x = 0, convective outflow
+    at x = nx - 1 (reading R27), walls top and bottom.  At steady state the
+    flow rate is the same in every column, the outlet pressure is the
+    reference, and the profile three quarters down the channel has the fully
+    developed power-law shape (2n+1)/(n+1) (1 - |y/H|^((n+1)/n)) times the mean
+    velocity of that column within the Table 2 error for the same n."""
+    table = _golden("paper_table2_channel.json")
+    bound = dict(zip(table["n"], table["E_rel"]))[n]
+    p, C, ux = inputs.open_channel_case(n, ny=ny)
+    nx, uin = p["nx"], p["u_in"]
+    o = oracle.Oracle(p)
+    o.set_fields(C, ux=ux)
+    prev = None
+    for _ in range(200):
+        o.step(250)
+        u = o.field("ux")
+        if prev is not None and np.linalg.norm(u - prev) / np.linalg.norm(u) < 1e-7:
+            break
+        prev = u
+    flux = u.sum(axis=0)
+    assert flux.max() / flux.min() - 1.0 < 1e-4
+    assert abs(o.field("p")[:, -1].mean()) < 1e-12
+    H = ny / 2.0
+    y = np.arange(ny) + 0.5 - H
+    col = u[:, 3 * nx // 4]
+    ua = col.mean() * (2 * n + 1) / (n + 1) * (1.0 - np.abs(y / H) ** ((n + 1) / n))
+    assert np.linalg.norm(col - ua) / np.linalg.norm(ua) <= bound          # Eq. 35
+    # the inlet delivers nearly the imposed velocity (the wall rows of the
+    # ghost column lose a few per cent)
+    assert 0.95 < col.mean() / uin <= 1.0
+    # the inflow carries the channel's own fluid: C moves by less than 1 % near
+    # the inlet, where the equilibrium h at the imposed velocity meets the
+    # slower wall rows
+    c = o.field("C1")
+    assert np.max(np.abs(c - 1.0)) < 1e-2 and np.mean(np.abs(c - 1.0)) < 2e-3
+
+
 # ------------------------------------------------------------------ P8
 def test_hydrostatic_pressure():
     """Gravity on a resting single phase between walls: p linear with slope -rho g."""
