@@ -341,11 +341,13 @@ cudaError_t launch_sweep_t(const DevParams &P, const FusedBuffers &B, cudaStream
 
 // Launch configurations of the row sweep: strip width x rows per pipeline
 // step / threads / minimum resident CTAs per SM.
-int sweep_variant_count(const DevParams &P) { return P.nh == 1 ? 6 : 3; }
+int sweep_variant_count(const DevParams &P) { return P.nh == 1 ? 13 : 4; }
 
 const char *sweep_variant_name(const DevParams &P, int v) {
-  static const char *n1[6] = {"64x2/160/3", "32x4/160/3", "128x1/160/2", "64x4/288/2", "64x1/96/5", "32x8/320/2"};
-  static const char *n2[3] = {"64x2/160/2", "32x4/160/2", "64x1/96/4"};
+  static const char *n1[13] = {"64x2/160/3", "32x4/160/3", "128x1/160/2", "64x4/288/2", "64x1/96/5",
+                               "32x8/320/2", "62x2/160/3", "126x1/160/2", "30x4/160/3", "60x2/160/3",
+                               "28x4/160/3", "58x2/128/3", "58x2/128/4"};
+  static const char *n2[4] = {"64x2/160/2", "32x4/160/2", "64x1/96/4", "62x2/160/2"};
   if (v < 0 || v >= sweep_variant_count(P)) v = 0;
   return P.nh == 1 ? n1[v] : n2[v];
 }
@@ -359,12 +361,23 @@ static cudaError_t sweep_dispatch(int v, const DevParams &P, const FusedBuffers 
       case 3: return launch_sweep_t<64, 4, NH, FORM, 288, 2>(P, B, s);
       case 4: return launch_sweep_t<64, 1, NH, FORM, 96, 5>(P, B, s);
       case 5: return launch_sweep_t<32, 8, NH, FORM, 320, 2>(P, B, s);
+      // strips whose collision rows are a whole number of warps (RS (TX + 2) = 128)
+      case 6: return launch_sweep_t<62, 2, NH, FORM, 160, 3>(P, B, s);
+      case 7: return launch_sweep_t<126, 1, NH, FORM, 160, 2>(P, B, s);
+      case 8: return launch_sweep_t<30, 4, NH, FORM, 160, 3>(P, B, s);
+      // ... and whose field rows are (RS (TX + 4) = 128)
+      case 9: return launch_sweep_t<60, 2, NH, FORM, 160, 3>(P, B, s);
+      case 10: return launch_sweep_t<28, 4, NH, FORM, 160, 3>(P, B, s);
+      // ... and whose order-parameter rows are (RS (TX + 6) = 128): four warps
+      case 11: return launch_sweep_t<58, 2, NH, FORM, 128, 3>(P, B, s);
+      case 12: return launch_sweep_t<58, 2, NH, FORM, 128, 4>(P, B, s);
       default: return launch_sweep_t<64, 2, NH, FORM, 160, 3>(P, B, s);
     }
   } else {
     switch (v) {
       case 1: return launch_sweep_t<32, 4, NH, FORM, 160, 2>(P, B, s);
       case 2: return launch_sweep_t<64, 1, NH, FORM, 96, 4>(P, B, s);
+      case 3: return launch_sweep_t<62, 2, NH, FORM, 160, 2>(P, B, s);
       default: return launch_sweep_t<64, 2, NH, FORM, 160, 2>(P, B, s);
     }
   }
