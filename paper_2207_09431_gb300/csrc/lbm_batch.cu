@@ -60,15 +60,17 @@ struct lbm_batch {
     for (auto *x : h) delete x;
   }
 
-  // Work list of the active, initialised cases for tile variant v; uploads it.
+  // Work list of the active, initialised cases for configuration v (tiles, or
+  // strips x row segments of a sweep); uploads it.
   cudaError_t build_work(int v, int *count) {
     std::vector<lbm::WorkItem> w;
     for (int i = 0; i < n; ++i) {
       if (!active[i] || !h[i]->initialized) continue;
       int tx = 32, ty = 8;
       lbm::batched_variant_tile(nh, v, &tx, &ty);
-      for (int y0 = 0; y0 < h[i]->dp.ny; y0 += ty)
-        for (int x0 = 0; x0 < h[i]->dp.nx; x0 += tx) w.push_back({i, x0, y0});
+      const int ny = h[i]->dp.ny;
+      for (int y0 = 0; y0 < ny; y0 += ty)
+        for (int x0 = 0; x0 < h[i]->dp.nx; x0 += tx) w.push_back({i, x0, y0, y0 + ty < ny ? y0 + ty : ny});
     }
     *count = (int)w.size();
     if (w.empty()) return cudaSuccess;

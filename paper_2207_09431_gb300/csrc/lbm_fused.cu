@@ -367,10 +367,18 @@ cudaError_t launch_fused_step(const DevParams &P, const FusedBuffers &B, cudaStr
   }
 }
 
-int batched_variant_count(int nh) { return nh == 1 ? VariantTable<1, 0>::kCount : VariantTable<2, 0>::kCount; }
+int batched_variant_count(int nh) {
+  return sweep_batched_count(nh) + (nh == 1 ? VariantTable<1, 0>::kCount : VariantTable<2, 0>::kCount);
+}
 
+bool batched_variant_is_sweep(int nh, int v) { return v >= 0 && v < sweep_batched_count(nh); }
+
+// Tile of configuration v (sweeps: strip width and segment rows).
 void batched_variant_tile(int nh, int v, int *tx, int *ty) {
   if (v < 0 || v >= batched_variant_count(nh)) v = 0;
+  const int ns = sweep_batched_count(nh);
+  if (v < ns) return sweep_batched_shape(nh, v, tx, ty);
+  v -= ns;
   if (nh == 1) VariantTable<1, 0>::tile(v, tx, ty);
   else VariantTable<2, 0>::tile(v, tx, ty);
 }
@@ -378,6 +386,9 @@ void batched_variant_tile(int nh, int v, int *tx, int *ty) {
 cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
                                 int parity, cudaStream_t s, int v) {
   if (v < 0 || v >= batched_variant_count(nh)) v = 0;
+  const int ns = sweep_batched_count(nh);
+  if (v < ns) return launch_sweep_batched(nh, collapse_h, cases, work, nwork, parity, s, v);
+  v -= ns;
   if (collapse_h) {
     if (nh == 1) return VariantTable<1, 1>::launch_batched(v, cases, work, nwork, parity, s);
     return VariantTable<2, 1>::launch_batched(v, cases, work, nwork, parity, s);

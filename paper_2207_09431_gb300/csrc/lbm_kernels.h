@@ -38,13 +38,19 @@ struct BatchCase {
 };
 // One CTA of a batched step: a case and the origin of one of its tiles.
 struct WorkItem {
-  int case_id, x0, y0;
+  int case_id, x0, y0, y1;  // y1: end row of a sweep segment (unused by tiles)
 };
 
 bool fused_supported(const DevParams &P);
-// Tile configurations of the batched step (work items are (case, tile)).
+// Configurations of the batched step: sweeps (work items (case, strip,
+// segment)) first, then tiles (work items (case, tile)).
 int batched_variant_count(int nh);
+bool batched_variant_is_sweep(int nh, int v);
 void batched_variant_tile(int nh, int v, int *tx, int *ty);
+int sweep_batched_count(int nh);
+void sweep_batched_shape(int nh, int v, int *tx, int *rows);
+cudaError_t launch_sweep_batched(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+                                 int parity, cudaStream_t s, int v);
 cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
                                 int parity, cudaStream_t s, int v);
 // Launch configurations of the fused step: row sweeps (strip width, rows per

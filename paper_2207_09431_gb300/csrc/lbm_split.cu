@@ -432,48 +432,66 @@ __global__ void k_init(DevParams P, const float *__restrict__ Cf, const float *_
 // FP64 observable sums of Sec. 3.1 and Eq. 43-44 over the current fields:
 // acc[0..10] = M1..3, M1..3 above 0.5, A, sum C_g x, sum C_g y, sum C_g ux,
 // sum C_g uy; ext[0..3] = xmin, -xmax, ymin, -ymax of C_g > 0.5 (atomicMin).
-__global__ void k_observables(DevParams P, const float *__restrict__ Cf, const float *__restrict__ uxf,
-                              const float *__restrict__ uyf, int gas_comp, double *acc, int *ext) {
-  int x, y;
-  const bool inside = node_of_thread(P, x, y);
+// Observable sums (Sec. 3.1; Eq. 43-44 inputs) in FP64: each thread walks
+// rows (a block per row, grid-stride) accumulating its nodes, then warp
+// shuffles, one shared-memory pass per block and one atomic per block and
+// quantity.
+constexpr int kObsThreads = 256;
+
+__global__ void __launch_bounds__(kObsThreads) k_observables(DevParams P, const float *__restrict__ Cf,
+                                                             const float *__restrict__ uxf,
+                                                             const float *__restrict__ uyf, int gas_comp,
+                                                             double *acc, int *ext) {
   double v[11];
   for (int q = 0; q < 11; ++q) v[q] = 0.0;
   int e[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
-  if (inside) {
-    const long long k = node_index(P, x, y);
-    float C[3];
-    CReader{Cf, P.plane, P.nh}.at(k, C);
-    for (int i = 0; i < 3; ++i) {
-      v[i] = C[i];
-      v[3 + i] = C[i] > 0.5f ? (double)C[i] : 0.0;
-    }
-    const double cg = C[gas_comp - 1];
-    v[6] = cg;
-    v[7] = cg * x;
-    v[8] = cg * y;
-    v[9] = cg * uxf[k];
-    v[10] = cg * uyf[k];
-    if (C[gas_comp - 1] > 0.5f) {
-      e[0] = x;
-      e[1] = -x;
-      e[2] = y;
-      e[3] = -y;
+  const CReader cr{Cf, P.plane, P.nh};
+  for (int y = blockIdx.x; y < P.ny; y += gridDim.x) {
+    for (int x = threadIdx.x; x < P.nx; x += blockDim.x) {
+      const long long k = node_index(P, x, y);
+      float C[3];
+      cr.at(k, C);
+      for (int i = 0; i < 3; ++i) {
+        v[i] += C[i];
+        v[3 + i] += C[i] > 0.5f ? (double)C[i] : 0.0;
+      }
+      const double cg = C[gas_comp - 1];
+      v[6] += cg;
+      v[7] += cg * x;
+      v[8] += cg * y;
+      v[9] += cg * uxf[k];
+      v[10] += cg * uyf[k];
+      if (C[gas_comp - 1] > 0.5f) {
+        e[0] = min(e[0], x);
+        e[1] = min(e[1], -x);
+        e[2] = min(e[2], y);
+        e[3] = min(e[3], -y);
+      }
     }
   }
-  // warp reduction, then one atomic per warp
   for (int off = 16; off > 0; off >>= 1) {
     for (int q = 0; q < 11; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
     for (int q = 0; q < 4; ++q) e[q] = min(e[q], __shfl_down_sync(0xffffffffu, e[q], off));
   }
-  const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  __shared__ double sv[kObsThreads / 32][11];
+  __shared__ int se[kObsThreads / 32][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) {
-    for (int q = 0; q < 11; ++q) atomicAdd(&acc[q], v[q]);
-    for (int q = 0; q < 4; ++q)
-      if (e[q] != 0x7fffffff) atomicMin(&ext[q], e[q]);
+    for (int q = 0; q < 11; ++q) sv[warp][q] = v[q];
+    for (int q = 0; q < 4; ++q) se[warp][q] = e[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < 11) {
+    double t = 0.0;
+    for (int w = 0; w < kObsThreads / 32; ++w) t += sv[w][threadIdx.x];
+    atomicAdd(&acc[threadIdx.x], t);
+  } else if (threadIdx.x >= 32 && threadIdx.x < 36) {
+    const int q = threadIdx.x - 32;
+    int m = 0x7fffffff;
+    for (int w = 0; w < kObsThreads / 32; ++w) m = min(m, se[w][q]);
+    if (m != 0x7fffffff) atomicMin(&ext[q], m);
   }
 }
-
-// ---------------------------------------------------------------- launchers
 
 static dim3 node_grid(const DevParams &P, dim3 blk) {
   return dim3((P.nx + blk.x - 1) / blk.x, (P.ny + blk.y - 1) / blk.y);
@@ -509,8 +527,8 @@ void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s) {
 
 void launch_observables(const DevParams &P, const StepBuffers &B, int gas_comp, double *acc, int *ext,
                         cudaStream_t s) {
-  const dim3 blk(32, 8);
-  k_observables<<<node_grid(P, blk), blk, 0, s>>>(P, B.C, B.ux, B.uy, gas_comp, acc, ext);
+  const int blocks = P.ny < 1216 ? P.ny : 1216;  // 8 per SM on 152 SMs, at most one per row
+  k_observables<<<blocks, kObsThreads, 0, s>>>(P, B.C, B.ux, B.uy, gas_comp, acc, ext);
 }
 
 }  // namespace lbm

@@ -64,18 +64,16 @@ __device__ __forceinline__ int slot(int r, int base) {
   return (int)((unsigned)(r - base) % (unsigned)D);
 }
 
-template <int TX, int RS, int NH, int FORM, int PER, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffers B, int seg_len) {
+// The sweep of one strip [x0, x0 + TX) over output rows [ys, ye).  PER: 0 walls
+// in y, 1 periodic y, 2 taken from P at run time (batches mix both).
+template <int TX, int RS, int NH, int FORM, int PER, int NT>
+__device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffers &B, int x0, int ys, int ye,
+                                           PipeSmem<TX, RS, NH> &s) {
   using S = PipeSmem<TX, RS, NH>;
   static_assert(NT >= RS * S::W3, "one item of every stage per thread");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S &s = *reinterpret_cast<S *>(smem_raw);
-  constexpr int per = PER;
+  const int per = PER == 2 ? P.periodic_y : PER;
   const int nx = P.nx, ny = P.ny, pitch = P.pitch;
   const long long plane = P.plane;
-  const int x0 = blockIdx.x * TX;
-  const int ys = blockIdx.y * seg_len;
-  const int ye = min(ys + seg_len, ny);
   const int t = threadIdx.x;
 
   // this thread's item of each stage: row offset within the step, column
@@ -282,6 +280,32 @@ __global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffe
   }
 }
 
+template <int TX, int RS, int NH, int FORM, int PER, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffers B, int seg_len) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ys = blockIdx.y * seg_len;
+  sweep_body<TX, RS, NH, FORM, PER, NT>(P, B, blockIdx.x * TX, ys, min(ys + seg_len, P.ny),
+                                        *reinterpret_cast<PipeSmem<TX, RS, NH> *>(smem_raw));
+}
+
+// Many lattices in one launch: CTA b sweeps work item b = (case, strip origin,
+// rows [y0, y1)); the case's parameters and buffers are staged in shared memory.
+// parity selects which of the case's two buffer sets is the input this step.
+template <int TX, int RS, int NH, int FORM, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_sweep_batched(const BatchCase *__restrict__ cases,
+                                                            const WorkItem *__restrict__ work, int parity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ DevParams sP;
+  __shared__ FusedBuffers sB;
+  const WorkItem w = work[blockIdx.x];
+  if (threadIdx.x == 0) {
+    sP = cases[w.case_id].P;
+    sB = cases[w.case_id].B[cases[w.case_id].base_parity ^ parity];
+  }
+  __syncthreads();
+  sweep_body<TX, RS, NH, FORM, 2, NT>(sP, sB, w.x0, w.y0, w.y1, *reinterpret_cast<PipeSmem<TX, RS, NH> *>(smem_raw));
+}
+
 // Segment length for a strip count: balances the waves of CTAs against the
 // per-segment overhead (3 + 2 + 1 extra rows of stages 0-2 at each end and
 // the steps that fill the pipeline).
@@ -381,6 +405,59 @@ static cudaError_t sweep_dispatch(int v, const DevParams &P, const FusedBuffers 
       default: return launch_sweep_t<64, 2, NH, FORM, 160, 2>(P, B, s);
     }
   }
+}
+
+// Batched sweeps (work items of the strip width and segment length of the
+// configuration; segments of 48 or 96 rows keep thousands of items for an
+// ensemble of small lattices).
+template <int TX, int RS, int NH, int FORM, int NT, int MINB>
+static cudaError_t launch_sweep_batched_t(const BatchCase *cases, const WorkItem *work, int nwork, int parity,
+                                          cudaStream_t st) {
+  const size_t smem = sizeof(PipeSmem<TX, RS, NH>);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_batched<TX, RS, NH, FORM, NT, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (nwork <= 0) return cudaSuccess;
+  k_sweep_batched<TX, RS, NH, FORM, NT, MINB><<<nwork, NT, smem, st>>>(cases, work, parity);
+  return cudaGetLastError();
+}
+
+int sweep_batched_count(int nh) { return nh == 1 ? 4 : 2; }
+
+void sweep_batched_shape(int nh, int v, int *tx, int *rows) {
+  static const int s1[4][2] = {{58, 48}, {58, 96}, {60, 48}, {64, 48}};
+  static const int s2[2][2] = {{64, 48}, {62, 48}};
+  if (v < 0 || v >= sweep_batched_count(nh)) v = 0;
+  *tx = nh == 1 ? s1[v][0] : s2[v][0];
+  *rows = nh == 1 ? s1[v][1] : s2[v][1];
+}
+
+template <int NH, int FORM>
+static cudaError_t sweep_batched_dispatch(int v, const BatchCase *c, const WorkItem *w, int n, int parity,
+                                          cudaStream_t s) {
+  if constexpr (NH == 1) {
+    switch (v) {
+      case 2: return launch_sweep_batched_t<60, 2, NH, FORM, 160, 3>(c, w, n, parity, s);
+      case 3: return launch_sweep_batched_t<64, 2, NH, FORM, 160, 3>(c, w, n, parity, s);
+      default: return launch_sweep_batched_t<58, 2, NH, FORM, 128, 3>(c, w, n, parity, s);
+    }
+  } else {
+    if (v == 1) return launch_sweep_batched_t<62, 2, NH, FORM, 160, 2>(c, w, n, parity, s);
+    return launch_sweep_batched_t<64, 2, NH, FORM, 160, 2>(c, w, n, parity, s);
+  }
+}
+
+cudaError_t launch_sweep_batched(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+                                 int parity, cudaStream_t s, int v) {
+  if (v < 0 || v >= sweep_batched_count(nh)) v = 0;
+  if (nh == 1) return collapse_h ? sweep_batched_dispatch<1, 1>(v, cases, work, nwork, parity, s)
+                                 : sweep_batched_dispatch<1, 0>(v, cases, work, nwork, parity, s);
+  return collapse_h ? sweep_batched_dispatch<2, 1>(v, cases, work, nwork, parity, s)
+                    : sweep_batched_dispatch<2, 0>(v, cases, work, nwork, parity, s);
 }
 
 cudaError_t launch_sweep_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v) {
