@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-from paper_2207_09431_gb300 import inputs  # noqa: E402
+from paper_2207_09431_gb300 import inputs, replicas  # noqa: E402
 
 METRIC = "coupled-step MLUPS (D2Q9, 2 components, FP32)"
 UNIT = "MLUPS"
@@ -225,10 +225,7 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = replicas.job_time_ms(ms, dist if world > 1 else None)
     value = world * nodes * args.steps / (ms_max * 1e-3) / 1e6
 
     # dominant kernel: per-kernel device time measured by the library on this stream
@@ -277,7 +274,7 @@ def run_ours(args):
         line["collapsed"] = run_state_form(args, torch, dev, stream, C, hbm, storage=0)
         line["fp16_storage"] = run_state_form(args, torch, dev, stream, C, hbm, storage=1)
     if not args.no_batched:
-        line["batched"] = run_batched(args, torch, dev, stream)
+        line["batched"] = run_batched(args, torch, dev, stream, rank, world, dist if world > 1 else None)
     if not args.no_surrogate and rank == 0:
         line["surrogate"] = run_surrogate(stream)
     if args.stability and rank == 0:
@@ -335,21 +332,22 @@ def run_state_form(args, torch, dev, stream, C, hbm, storage):
 STEPS_TO_TERMINAL = 50000  # time steps a rising-bubble case needs to reach its terminal velocity
 
 
-def run_batched(args, torch, dev, stream):
+def run_batched(args, torch, dev, stream, rank=0, world=1, dist=None):
     """The ensemble workload: seeded rising-bubble cases on grids from
     {100x200, 150x300, 200x400, 300x600}, advanced (a) together, one launch per
-    step over a (case, tile) work list replayed from a CUDA graph, and (b) one
-    case after another with lbm_step.  Both run the same kernel body, so the
+    step over a work list replayed from a CUDA graph, and (b) one case after
+    another with lbm_step.  Both run the same per-node arithmetic, so the
     terminal-velocity error is the same; cases/hour assumes STEPS_TO_TERMINAL
-    steps per case."""
+    steps per case.  With several ranks every rank takes its share of the
+    cases and the times are the slowest rank's."""
     from paper_2207_09431_gb300 import lbm
 
-    cases = inputs.ensemble_cases(args.batch_cases, seed=0)
+    all_cases = inputs.ensemble_cases(args.batch_cases, seed=0)
+    cases = replicas.shard(all_cases, rank, world)
     batch = lbm.Batch([c[0] for c in cases], device=dev, stream=stream)
-    nodes = 0
+    nodes = sum(p["nx"] * p["ny"] for p, _, _ in all_cases)
     for i, (p, b, _) in enumerate(cases):
         batch.case(i).set_fields(inputs.bubble_fields(p["nx"], p["ny"], 2, p["xi"], b, seed=i, noise=1e-8))
-        nodes += p["nx"] * p["ny"]
     chosen = batch.autotune(reps=3)
     K = max(16, (args.steps // 16) * 16)
     batch.step(16)
@@ -359,7 +357,7 @@ def run_batched(args, torch, dev, stream):
     batch.step(K)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
-    ms_batch = ev0.elapsed_time(ev1) / K
+    ms_batch = replicas.job_time_ms(ev0.elapsed_time(ev1) / K, dist)
     # one case after another: the same handles through lbm_step
     handles = [batch.case(i).h for i in range(len(cases))]
     for h in handles:
@@ -371,15 +369,16 @@ def run_batched(args, torch, dev, stream):
         lbm.lbm_step(h, Kc)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
-    ms_single = ev0.elapsed_time(ev1) / Kc
+    ms_single = replicas.job_time_ms(ev0.elapsed_time(ev1) / Kc, dist)
     hours_batch = STEPS_TO_TERMINAL * ms_batch / 3.6e6
     hours_single = STEPS_TO_TERMINAL * ms_single / 3.6e6
-    return {"cases": len(cases), "nodes": nodes, "density_ratio": cases[0][0]["rho"][0] / cases[0][0]["rho"][2],
+    return {"cases": len(all_cases), "nodes": nodes, "ranks": world,
+            "density_ratio": all_cases[0][0]["rho"][0] / all_cases[0][0]["rho"][2],
             "ms_per_step": round(ms_batch, 4), "mlups": round(nodes / (ms_batch * 1e3), 1),
             "per_case_ms_per_step": round(ms_single, 4), "per_case_mlups": round(nodes / (ms_single * 1e3), 1),
             "speedup": round(ms_single / ms_batch, 3), "steps_to_terminal_assumed": STEPS_TO_TERMINAL,
-            "cases_per_hour": round(len(cases) / hours_batch, 1),
-            "per_case_cases_per_hour": round(len(cases) / hours_single, 1),
+            "cases_per_hour": round(len(all_cases) / hours_batch, 1),
+            "per_case_cases_per_hour": round(len(all_cases) / hours_single, 1),
             "kernel_config": chosen, "graph_steps": 16}
 
 
