@@ -176,36 +176,58 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
       }
     }
   }
-  // equilibria and forcing of every direction, h*, momentum flux of g - g^eq
+  // Per direction a, with Gamma_a = w_a T_a, T_a = 1 - 1.5 u.u + 4.5 (e.u)^2 + 3 e.u:
+  //   E_a   = (e_a - u).(F_s + F_b) = sum_i (mu_i - mu_3) d_a C_i + e_a.F_b - u.F
+  //   ph_a  = (d_a rho - u.grad rho) cs^2 (Gamma_a - w_a) + E_a Gamma_a        (Eq. 14-16)
+  //   geq_a = w_a p + rho cs^2 (Gamma_a - w_a) - ph_a / 2
+  //   h*_a  = C_i Gamma_a + [d_a C_i - u.grad C_i
+  //            - C_i/(rho cs^2) (d_a p - u.grad p - E_a)] Gamma_a / 2 + S_i Gamma_a / 2   (Eq. 18-20)
+  // e.u, e.F_b and the directional derivatives change sign between opposite
+  // directions, (e.u)^2 does not: those are formed once per pair.
+  const float S0 = 1.0f - 1.5f * uu;
+  const float uF = udFs + udFb;
+  const float udr3 = udr * kCs2;
+  float euv[9], Bv[9], Xv[9];
+  euv[0] = 0.f;
+  Bv[0] = S0;
+  Xv[0] = 0.f;
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    if (a == 1 || a == 2 || a == 5 || a == 6) {
+      const float eu = ex(a) * ux + ey(a) * uy;
+      const float Bp = fmaf(4.5f * eu, eu, S0);
+      float X = ex(a) * P.force_x + ey(a) * Fby;
+#pragma unroll
+      for (int i = 0; i < NH; ++i) X = fmaf(c.dmu[i], dCv[i][a], X);
+      euv[a] = eu;
+      euv[opp(a)] = -eu;
+      Bv[a] = Bv[opp(a)] = Bp;
+      Xv[a] = X;
+      Xv[opp(a)] = -X;
+    }
+  }
   float eqf[9];
   float Pxx = 0.f, Pyy = 0.f, Pxy = 0.f;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
     const float exa = (float)ex(a), eya = (float)ey(a), w = wt(a);
-    const float eu = exa * ux + eya * uy;
-    const float G = w * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-    const float dr = drv[a];
-    const float dp = dpv[a];
-    float dC[NH];
-    float eFs = -udFs;
-#pragma unroll
-    for (int i = 0; i < NH; ++i) {
-      dC[i] = dCv[i][a];
-      eFs += c.dmu[i] * dC[i];
-    }
-    const float eFb = exa * P.force_x + eya * Fby - udFb;
-    const float ph = (dr - udr) * kCs2 * (G - w) + (eFs + eFb) * G;
-    const float geq = w * p + rcs2 * (G - w) - 0.5f * ph;
+    const float G = w * fmaf(3.0f, euv[a], Bv[a]);
+    const float Gw = G - w;
+    const float E = Xv[a] - uF;
+    const float ph = fmaf(fmaf(drv[a], kCs2, -udr3), Gw, E * G);
+    const float geq = fmaf(-0.5f, ph, fmaf(rcs2, Gw, w * p));
     const float fneq = g[a] - geq;
     g[a] = fneq;
     eqf[a] = geq + ph;
     Pxx += fneq * exa * exa;
     Pyy += fneq * eya * eya;
     Pxy += fneq * exa * eya;
-    const float ep = dp - udp - eFs - eFb;
+    const float ep = (dpv[a] - udp) - E;
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
-      const float phh = (dC[i] - udC[i] - kap[i] * ep) * G;
+      // C_i Gamma kept as its own term: the small corrections are not rounded
+      // into a value of the size of C_i first
+      const float phh = (dCv[i][a] - udC[i] - kap[i] * ep) * G;
       hs[i][a] = Cc[i] * G + 0.5f * phh + 0.5f * sv[i] * G;
     }
   }
