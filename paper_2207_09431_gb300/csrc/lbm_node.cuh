@@ -244,14 +244,6 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
   for (int a = 0; a < 9; ++a) g[a] = (1.0f - om) * g[a] + eqf[a];
 }
 
-// Equilibrium weight Gamma_a at the arrival node for the destination-side
-// term of Eq. 18 (reading R9).
-__device__ __forceinline__ float node_gamma(int a, float ux, float uy) {
-  const float eu = ex(a) * ux + ey(a) * uy;
-  const float uu = ux * ux + uy * uy;
-  return wt(a) * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-}
-
 // FP16 deviation codec of the FP16 storage form: g_a is kept as
 // half((g_a - w_a P) scale) with P = sum_a g_a in FP32.  One rounding order for
 // every encoder and decoder, so that a decode-encode round trip is exact.
@@ -337,11 +329,27 @@ __device__ __forceinline__ void store_node(const DevParams &P, const FusedBuffer
     for (int a = 0; a < 9; ++a) B.g_out[(long long)a * plane + ky] = gy[a];
   }
   if constexpr (FORM == 0) {
+    // Gamma_a = w_a (1 - 1.5 u.u + 4.5 (e.u)^2 + 3 e.u): the even part is shared
+    // by opposite directions
+    const float S0 = 1.0f - 1.5f * (ux * ux + uy * uy);
+    float G[9];
+    G[0] = wt(0) * S0;
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+      if (a == 1 || a == 2 || a == 5 || a == 6) {
+        const float eu = ex(a) * ux + ey(a) * uy;
+        const float Bp = fmaf(4.5f * eu, eu, S0);
+        G[a] = wt(a) * fmaf(3.0f, eu, Bp);
+        G[opp(a)] = wt(a) * fmaf(-3.0f, eu, Bp);
+      }
+    }
+    float hsv[NH];
+#pragma unroll
+    for (int i = 0; i < NH; ++i) hsv[i] = 0.5f * sv[i];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      const float G = node_gamma(a, ux, uy);
 #pragma unroll
-      for (int i = 0; i < NH; ++i) B.h_out[((long long)i * 9 + a) * plane + ky] = hy[i][a] + 0.5f * sv[i] * G;
+      for (int i = 0; i < NH; ++i) B.h_out[((long long)i * 9 + a) * plane + ky] = fmaf(hsv[i], G[a], hy[i][a]);
     }
   } else {
 #pragma unroll
