@@ -185,7 +185,8 @@ const char *lbm_kernel_name(const lbm_handle *h, int i);
  * CTA, CTAs per SM) for `reps` launches from the current state into the spare
  * buffer, without advancing the state, and keeps the fastest for lbm_step.
  * chosen (may be NULL) receives its index; lbm_kernel_name reports its name.
- * Synchronises the stream.  Handles start with configuration 0. */
+ * Synchronises the stream.  A handle starts with the row sweep measured
+ * fastest on the 2048 x 4096 rising bubble (its name through lbm_kernel_name). */
 lbm_status lbm_autotune(lbm_handle *h, int reps, int *chosen);
 
 /* Number of launch configurations of the step, and explicit selection of one

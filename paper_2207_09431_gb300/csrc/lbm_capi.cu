@@ -97,7 +97,7 @@ lbm_status lbm_create(const lbm_params *p, void *dev_arena, size_t arena_bytes, 
   // plane stride used by the kernels must match the arena planes
   h->dp.plane = (long long)pf;
   h->cur = 0;
-  h->variant = 0;
+  h->variant = h->fused() ? lbm::sweep_default_variant(h->dp) : 0;
   h->initialized = false;
   h->step = 0;
   h->have_prev = false;

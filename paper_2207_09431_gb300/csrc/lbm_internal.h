@@ -171,7 +171,7 @@ struct lbm_handle {
   int *ext;
   unsigned *err;
   int cur;
-  int variant;            // fused-step launch configuration (autotuned or 0)
+  int variant;            // fused-step launch configuration (autotuned or the default)
   std::string kname;      // name reported by lbm_kernel_name
   bool initialized;
   long long step;

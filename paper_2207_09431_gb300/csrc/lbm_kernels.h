@@ -57,6 +57,9 @@ cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases,
 // pipeline step, threads, CTAs per SM), then tiles (tile, threads, CTAs per SM).
 int sweep_variant_count(const DevParams &P);
 const char *sweep_variant_name(const DevParams &P, int v);
+// Configuration a handle starts with: the sweep that measured fastest on the
+// 2048 x 4096 rising bubble (58 x 2 strips, 128 threads, 3 CTAs per SM).
+int sweep_default_variant(const DevParams &P);
 cudaError_t launch_sweep_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v);
 int fused_variant_count(const DevParams &P);
 const char *fused_variant_name(const DevParams &P, int v);

@@ -367,6 +367,8 @@ cudaError_t launch_sweep_t(const DevParams &P, const FusedBuffers &B, cudaStream
 // step / threads / minimum resident CTAs per SM.
 int sweep_variant_count(const DevParams &P) { return P.nh == 1 ? 13 : 4; }
 
+int sweep_default_variant(const DevParams &P) { return P.nh == 1 ? 11 : 0; }
+
 const char *sweep_variant_name(const DevParams &P, int v) {
   static const char *n1[13] = {"64x2/160/3", "32x4/160/3", "128x1/160/2", "64x4/288/2", "64x1/96/5",
                                "32x8/320/2", "62x2/160/3", "126x1/160/2", "30x4/160/3", "60x2/160/3",
