@@ -37,32 +37,60 @@ namespace lbm {
 
 namespace {
 
+// Ring records: (C_1 .. C_NH, rho) and (mu_1 .. mu_NH, p) are one vector each,
+// so that a stencil point costs one shared-memory access.
+template <int NH>
+struct PairVec;
+template <>
+struct PairVec<1> {
+  using T = float2;
+  static __device__ __forceinline__ T make(const float *c, float last) { return make_float2(c[0], last); }
+  static __device__ __forceinline__ float comp(const T &v, int) { return v.x; }
+  static __device__ __forceinline__ float last(const T &v) { return v.y; }
+};
+template <>
+struct PairVec<2> {
+  using T = float4;
+  static __device__ __forceinline__ T make(const float *c, float last) { return make_float4(c[0], c[1], last, 0.f); }
+  static __device__ __forceinline__ float comp(const T &v, int q) { return q == 0 ? v.x : v.y; }
+  static __device__ __forceinline__ float last(const T &v) { return v.z; }
+};
+
 template <int TX, int RS, int NH>
 struct PipeSmem {
+  using PV = PairVec<NH>;
+  using V = typename PV::T;
   static constexpr int W3 = TX + 6, W2 = TX + 4, W1 = TX + 2;
   // ring depths: rows alive at once (written this step or read this step)
   static constexpr int D3 = 3 * RS + 3, D2 = 2 * RS + 2, DA = 2 * RS + 1, DB = 2 * RS + 2;
-  float C[NH][D3][W3];
-  float rho[D3][W3];
-  float mu[NH][D2][W2];
-  float p[D2][W2];
-  // stage 1 -> stage 2 (1-ring columns): g and the fields the collision
-  // needs at its own node
-  float g[9][DA][W1];
-  float ux[DA][W1], uy[DA][W1];
-  float dmu[NH][DA][W1], gCx[NH][DA][W1], gCy[NH][DA][W1];
-  float grx[DA][W1], gry[DA][W1];
-  // stage 2 -> stage 3: g*, h*, sources and the velocity of the node
+  // stage 1 -> stage 2 record of a 1-ring node, in float4 words: g_0..g_8,
+  // u_x, u_y, grad rho, then mu_i - mu_3, d_x C_i, d_y C_i per component
+  static constexpr int NR = 13 + 3 * NH, NQ = (NR + 3) / 4;
+  float4 da[NQ][DA][W1];
+  V cr[D3][W3];  // (C_i, rho) of the 3-ring
+  V mp[D2][W2];  // (mu_i, p) of the 2-ring
+  // stage 2 -> stage 3: velocity of the collision node, g*, h*, sources
+  float2 uvb[DB][W1];
   float gs[9][DB][W1];
   float hs[NH][9][DB][W1];
-  float sv[NH][DB][W1];
-  float uxb[DB][W1], uyb[DB][W1];
+  float svb[NH][DB][W1];
 };
 
-template <int D>
-__device__ __forceinline__ int slot(int r, int base) {
-  return (int)((unsigned)(r - base) % (unsigned)D);
+// Ring slot arithmetic: every thread's rows move up RS rows per step, so its
+// slots are kept in registers and advanced, and the slots of the rows next to
+// a slot are one step around the ring.
+template <int D, int N>
+__device__ __forceinline__ int ring_add(int s) {
+  static_assert(N < D, "advance within one turn of the ring");
+  s += N;
+  return s >= D ? s - D : s;
 }
+template <int D>
+__device__ __forceinline__ int ring_up(int s) { return s == D - 1 ? 0 : s + 1; }
+template <int D>
+__device__ __forceinline__ int ring_dn(int s) { return s == 0 ? D - 1 : s - 1; }
+// slot of row r + ey from those of rows r - 1, r, r + 1
+__device__ __forceinline__ int row_slot(int dy, int sdn, int s, int sup) { return dy < 0 ? sdn : (dy > 0 ? sup : s); }
 
 // The sweep of one strip [x0, x0 + TX) over output rows [ys, ye).  PER: 0 walls
 // in y, 1 periodic y, 2 taken from P at run time (batches mix both).
@@ -70,6 +98,8 @@ template <int TX, int RS, int NH, int FORM, int PER, int NT>
 __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffers &B, int x0, int ys, int ye,
                                            PipeSmem<TX, RS, NH> &s) {
   using S = PipeSmem<TX, RS, NH>;
+  using PV = typename S::PV;
+  using V = typename S::V;
   static_assert(NT >= RS * S::W3, "one item of every stage per thread");
   const int per = PER == 2 ? P.periodic_y : PER;
   const int nx = P.nx, ny = P.ny, pitch = P.pitch;
@@ -91,7 +121,14 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
 
   // first step: stage 0 starts at row ys - 3, and j stays aligned with ys
   const int j0 = ys - 3 * RS - RS * ((6 + RS - 1) / RS);
-  const int base = j0;  // ring rows are counted from here (all rows used are >= base)
+  // Ring rows are counted from j0: the slot of row r in a ring of depth D is
+  // (r - j0) mod D.  The slots of this thread's rows at the first step:
+  int s0 = (3 * RS + 3 + d0) % S::D3;                                        // stage 0 row
+  int s1c = (2 * RS + 2 + d1) % S::D3, s1m = (2 * RS + 2 + d1) % S::D2;      // stage 1 row
+  int s1a = (2 * RS + 2 + d1) % S::DA;
+  int s2c = (RS + 1 + d2) % S::D3, s2m = (RS + 1 + d2) % S::D2;              // stage 2 row
+  int s2a = (RS + 1 + d2) % S::DA, s2b = (RS + 1 + d2) % S::DB;
+  int s3 = d3 % S::DB;                                                       // stage 3 row
 
   // Global loads run one pipeline step ahead: the values a step consumes were
   // requested during the previous step, so their latency overlaps a whole
@@ -158,10 +195,7 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
           cst[q] = nh[q];
         }
       }
-      const int sc = slot<S::D3>(r0, base);
-#pragma unroll
-      for (int q = 0; q < NH; ++q) s.C[q][sc][c0] = cst[q];
-      s.rho[sc][c0] = node_rho<NH>(P, cst);
+      s.cr[s0][c0] = PV::make(cst, node_rho<NH>(P, cst));
     }
 
     // ---- stage 1: fields of row r1 (2-ring column c1)
@@ -172,34 +206,37 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
         if constexpr (FORM == 2) gv[a] = g16_decode(nP, ngh[a], a, P.g16_inv_scale);
         else gv[a] = ng[a];
       }
+      const int cdn = ring_dn<S::D3>(s1c), cup = ring_up<S::D3>(s1c);
       float cn[NH][9], rn[9];
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        const int sc = slot<S::D3>(r1 + ey(a), base);
+        const V v = s.cr[row_slot(ey(a), cdn, s1c, cup)][c1 + 1 + ex(a)];
 #pragma unroll
-        for (int q = 0; q < NH; ++q) cn[q][a] = s.C[q][sc][c1 + 1 + ex(a)];
-        rn[a] = s.rho[sc][c1 + 1 + ex(a)];
+        for (int q = 0; q < NH; ++q) cn[q][a] = PV::comp(v, q);
+        rn[a] = PV::last(v);
       }
       NodeFields f;
       node_fields<NH>(P, gv, cn, rn, f);
-      const int sm = slot<S::D2>(r1, base);
-#pragma unroll
-      for (int q = 0; q < NH; ++q) s.mu[q][sm][c1] = f.mu[q];
-      s.p[sm][c1] = f.p;
+      s.mp[s1m][c1] = PV::make(f.mu, f.p);
       if (c1 >= 1 && c1 <= TX + 2) {
-        const int sa = slot<S::DA>(r1, base), cc = c1 - 1;
+        float rec[4 * S::NQ];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) s.g[a][sa][cc] = gv[a];
+        for (int a = 0; a < 9; ++a) rec[a] = gv[a];
+        rec[9] = f.ux;
+        rec[10] = f.uy;
+        rec[11] = f.rx;
+        rec[12] = f.ry;
 #pragma unroll
         for (int q = 0; q < NH; ++q) {
-          s.dmu[q][sa][cc] = f.mu[q] - f.mu[2];
-          s.gCx[q][sa][cc] = f.gCx[q];
-          s.gCy[q][sa][cc] = f.gCy[q];
+          rec[13 + q] = f.mu[q] - f.mu[2];
+          rec[13 + NH + q] = f.gCx[q];
+          rec[13 + 2 * NH + q] = f.gCy[q];
         }
-        s.ux[sa][cc] = f.ux;
-        s.uy[sa][cc] = f.uy;
-        s.grx[sa][cc] = f.rx;
-        s.gry[sa][cc] = f.ry;
+#pragma unroll
+        for (int k = S::NR; k < 4 * S::NQ; ++k) rec[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < S::NQ; ++k)
+          s.da[k][s1a][c1 - 1] = make_float4(rec[4 * k], rec[4 * k + 1], rec[4 * k + 2], rec[4 * k + 3]);
       }
     }
     const float tprev = nt;
@@ -207,75 +244,107 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
 
     // ---- stage 3: arriving populations of output row r3
     if (a3) {
-      const int sb = slot<S::DB>(r3, base);
+      const int sdn = ring_dn<S::DB>(s3), sup = ring_up<S::DB>(s3);
       float gy[9], hy[NH][9], svy[NH];
 #pragma unroll
-      for (int q = 0; q < NH; ++q) svy[q] = s.sv[q][sb][c3 + 1];
+      for (int q = 0; q < NH; ++q) svy[q] = s.svb[q][s3][c3 + 1];
+      const float2 uv = s.uvb[s3][c3 + 1];
+      if (per || (j >= 1 && j + RS <= ny - 1)) {
+        // no output row of this step is next to a wall
 #pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        int src = r3 - ey(a), cs = c3 + 1 - ex(a), b = a;
-        if (!per && (src < 0 || src >= ny)) {  // half-way bounce-back: the population left r3 in -e_a
-          src = r3;
-          cs = c3 + 1;
-          b = opp(a);
+        for (int a = 0; a < 9; ++a) {
+          const int ss = row_slot(-ey(a), sdn, s3, sup), cs = c3 + 1 - ex(a);  // source row r3 - e_a
+          gy[a] = s.gs[a][ss][cs];
+#pragma unroll
+          for (int q = 0; q < NH; ++q) hy[q][a] = s.hs[q][a][ss][cs];
         }
-        const int ss = slot<S::DB>(src, base);
-        gy[a] = s.gs[b][ss][cs];
+      } else {
+        const bool lo = r3 == 0, hi = r3 == ny - 1;
 #pragma unroll
-        for (int q = 0; q < NH; ++q) hy[q][a] = s.hs[q][b][ss][cs];
+        for (int a = 0; a < 9; ++a) {
+          // half-way bounce-back: a source row beyond the wall means the
+          // population left r3 in -e_a
+          const bool bb = (ey(a) > 0 && lo) || (ey(a) < 0 && hi);
+          const int ss = bb ? s3 : row_slot(-ey(a), sdn, s3, sup);
+          const int cs = bb ? c3 + 1 : c3 + 1 - ex(a);
+          const int b = bb ? opp(a) : a;
+          gy[a] = s.gs[b][ss][cs];
+#pragma unroll
+          for (int q = 0; q < NH; ++q) hy[q][a] = s.hs[q][b][ss][cs];
+        }
       }
-      store_node<NH, FORM>(P, B, plane, (long long)r3 * pitch + x3, gy, hy, svy, s.uxb[sb][c3 + 1],
-                           s.uyb[sb][c3 + 1]);
+      store_node<NH, FORM>(P, B, plane, (long long)r3 * pitch + x3, gy, hy, svy, uv.x, uv.y);
     }
 
     // ---- stage 2: collision of row r2 (1-ring column c2)
     if (a2) {
-      const int sa = slot<S::DA>(r2, base), sb = slot<S::DB>(r2, base);
+      const int cdn = ring_dn<S::D3>(s2c), cup = ring_up<S::D3>(s2c);
+      int mdn = ring_dn<S::D2>(s2m), mup = ring_up<S::D2>(s2m);
+      if (!per) {
+        // mu and p one row beyond a wall: the mirror row is row r2 itself
+        if (r2 == 0) mdn = s2m;
+        if (r2 == ny - 1) mup = s2m;
+      }
       float pn[9], rn[9], cn[NH][9], mun[NH][9], g2[9];
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        // mu and p one row beyond a wall: the mirror row is row r2 itself
-        int rm = r2 + ey(a);
-        if (!per) rm = rm < 0 ? 0 : (rm >= ny ? ny - 1 : rm);
-        const int sm = slot<S::D2>(rm, base);
-        const int sc = slot<S::D3>(r2 + ey(a), base);
-        pn[a] = s.p[sm][c2 + 1 + ex(a)];
-        rn[a] = s.rho[sc][c2 + 2 + ex(a)];
-        g2[a] = s.g[a][sa][c2];
+        const V cr = s.cr[row_slot(ey(a), cdn, s2c, cup)][c2 + 2 + ex(a)];
+        const V mp = s.mp[row_slot(ey(a), mdn, s2m, mup)][c2 + 1 + ex(a)];
+        pn[a] = PV::last(mp);
+        rn[a] = PV::last(cr);
 #pragma unroll
         for (int q = 0; q < NH; ++q) {
-          cn[q][a] = s.C[q][sc][c2 + 2 + ex(a)];
-          mun[q][a] = s.mu[q][sm][c2 + 1 + ex(a)];
+          cn[q][a] = PV::comp(cr, q);
+          mun[q][a] = PV::comp(mp, q);
         }
       }
+      float rec[4 * S::NQ];
+#pragma unroll
+      for (int k = 0; k < S::NQ; ++k) {
+        const float4 w = s.da[k][s2a][c2];
+        rec[4 * k] = w.x;
+        rec[4 * k + 1] = w.y;
+        rec[4 * k + 2] = w.z;
+        rec[4 * k + 3] = w.w;
+      }
+#pragma unroll
+      for (int a = 0; a < 9; ++a) g2[a] = rec[a];
       NodeCenter nc;
-      nc.ux = s.ux[sa][c2];
-      nc.uy = s.uy[sa][c2];
+      nc.ux = rec[9];
+      nc.uy = rec[10];
+      nc.grx = rec[11];
+      nc.gry = rec[12];
       nc.p = pn[0];
       nc.rho = rn[0];
-      nc.grx = s.grx[sa][c2];
-      nc.gry = s.gry[sa][c2];
 #pragma unroll
       for (int q = 0; q < NH; ++q) {
-        nc.dmu[q] = s.dmu[q][sa][c2];
-        nc.gCx[q] = s.gCx[q][sa][c2];
-        nc.gCy[q] = s.gCy[q][sa][c2];
+        nc.dmu[q] = rec[13 + q];
+        nc.gCx[q] = rec[13 + NH + q];
+        nc.gCy[q] = rec[13 + 2 * NH + q];
       }
       float hs[NH][9], sv[NH], tn, gd2;
       node_collide<NH>(P, nc, pn, rn, cn, mun, g2, tprev, hs, sv, tn, gd2);
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        s.gs[a][sb][c2] = g2[a];
+        s.gs[a][s2b][c2] = g2[a];
 #pragma unroll
-        for (int q = 0; q < NH; ++q) s.hs[q][a][sb][c2] = hs[q][a];
+        for (int q = 0; q < NH; ++q) s.hs[q][a][s2b][c2] = hs[q][a];
       }
 #pragma unroll
-      for (int q = 0; q < NH; ++q) s.sv[q][sb][c2] = sv[q];
-      s.uxb[sb][c2] = nc.ux;
-      s.uyb[sb][c2] = nc.uy;
+      for (int q = 0; q < NH; ++q) s.svb[q][s2b][c2] = sv[q];
+      s.uvb[s2b][c2] = make_float2(nc.ux, nc.uy);
       if (own2 && r2 >= ys && r2 < ye) store_diagnostics<NH>(B, plane, k2, tn, gd2, sv, nc);
     }
 
+    s0 = ring_add<S::D3, RS>(s0);
+    s1c = ring_add<S::D3, RS>(s1c);
+    s1m = ring_add<S::D2, RS>(s1m);
+    s1a = ring_add<S::DA, RS>(s1a);
+    s2c = ring_add<S::D3, RS>(s2c);
+    s2m = ring_add<S::D2, RS>(s2m);
+    s2a = ring_add<S::DA, RS>(s2a);
+    s2b = ring_add<S::DB, RS>(s2b);
+    s3 = ring_add<S::DB, RS>(s3);
     __syncthreads();
   }
 }
