@@ -38,7 +38,7 @@ UNIT = "MLUPS"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nx", type=int, default=2048)
@@ -62,42 +62,63 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons.  Started and
+    awaited before the warm-up, so that its start-up does not overlap the
+    timed region; only the samples taken inside the timed window count."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.window = None
 
-    def start(self):
+    def start(self, wait_s=15.0):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.INTERVAL_MS)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t_end = time.perf_counter() + wait_s
+        while not self.lines and time.perf_counter() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def begin(self):
+        self.window = [time.perf_counter(), None]
+
+    def end(self):
+        if self.window is not None:
+            self.window[1] = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(self.INTERVAL_MS * 1.5e-3)   # the sample that closes the window
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        lines = self.lines
+        if self.window is not None and self.window[1] is not None:
+            t0, t1 = self.window[0], self.window[1] + self.INTERVAL_MS * 1e-3
+            inside = [x for x in lines if t0 <= x[0] <= t1]
+            lines = inside or lines[-1:]
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for _, line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -205,22 +226,21 @@ def run_ours(args):
         kernel_config = lbm.lbm_kernel_name(lat.h, 0)
     else:
         kernel_config = lat.autotune(reps=5)
-    lat.step(args.warmup)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
     clocks = ClockSampler(gpu_id_for_smi(local, torch))
     clocks.start()
+    lat.step(args.warmup)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
+    clocks.begin()
     with torch.cuda.stream(stream):
         ev0.record(stream)
         lat.step(args.steps)
         ev1.record(stream)
     torch.cuda.synchronize(dev)
+    clocks.end()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
@@ -434,7 +454,12 @@ def run_reference(args):
     p, C, desc = oracle_window(args.nx)
     o = oracle.Oracle(p)
     o.set_fields(C)
-    sub = 20  # lattice steps per bench step (bounded sample)
+    # lattice steps per bench step: a bounded sample, sized so that the whole
+    # run (warm-up and timed steps) takes about 150 s of host time
+    t0 = time.perf_counter()
+    o.step(1)
+    t_one = time.perf_counter() - t0
+    sub = max(1, int(150.0 / (max(args.steps + args.warmup, 1) * max(t_one, 1e-6))))
     o.step(args.warmup * sub)
     t0 = time.perf_counter()
     o.step(args.steps * sub)

@@ -93,6 +93,26 @@ __device__ __forceinline__ void chem_potentials(const DevParams &P, const float 
   mu[2] = P.mu_pre * ((d2 - d0) * P.inv_sig[0] + (d2 - d1) * P.inv_sig[1]) - P.grad_coef[2] * lapC[2];
 }
 
+// Two-component forms (C_2 = 0 identically): the same values as rho_of,
+// chem_potentials and tau_mix with C_2 = 0, without the terms that vanish
+// with C_2 (products with a constant zero are kept by IEEE arithmetic).
+__device__ __forceinline__ float rho_of2(const DevParams &P, float C1, float C3) {
+  const float c0 = fminf(fmaxf(C1, 0.0f), 1.0f), c2 = fminf(fmaxf(C3, 0.0f), 1.0f);
+  const float inv = __fdividef(1.0f, c0 + c2);
+  return (c0 * inv) * P.rho[0] + (c2 * inv) * P.rho[2];
+}
+
+// mu_1 and mu_3 of Eq. 5 with C_2 = 0: dE0/dC_1 = 2 Sigma_13 C_1 C_3^2,
+// dE0/dC_2 = C_1 C_3 (Sigma_1 C_1 + Sigma_3 C_3), dE0/dC_3 = 2 Sigma_13 C_1^2 C_3.
+__device__ __forceinline__ void chem_potentials2(const DevParams &P, float C1, float C3, float lap1, float lap3,
+                                                 float &mu1, float &mu3) {
+  const float mix = P.Sig[0] * C1 + P.Sig[2] * C3;
+  const float c13 = C1 * C3, s = 2.f * P.sig13 * c13;
+  const float d0 = s * C3, d1 = c13 * mix, d2 = s * C1;
+  mu1 = P.mu_pre * ((d0 - d1) * P.inv_sig[1] + (d0 - d2) * P.inv_sig[2]) - P.grad_coef[0] * lap1;
+  mu3 = P.mu_pre * ((d2 - d0) * P.inv_sig[0] + (d2 - d1) * P.inv_sig[1]) - P.grad_coef[2] * lap3;
+}
+
 // Power-law relaxation time at strain rate gd (Eq. 31-33, reading R4):
 // tau = k gd^(n-1) / (rho cs^2), clamped; irho = 1 / rho.
 __device__ __forceinline__ float tau_powerlaw(const DevParams &P, float gd, float irho) {
@@ -123,6 +143,12 @@ __device__ __forceinline__ float tau_mix(const DevParams &P, float C1, float C2,
   float c[3];
   mixture_weights(C1, C2, C3, c);
   return c[0] * tau1 + c[1] * P.tau[1] + c[2] * P.tau[2];
+}
+
+__device__ __forceinline__ float tau_mix2(const DevParams &P, float C1, float C3, float tau1) {
+  const float c0 = fminf(fmaxf(C1, 0.0f), 1.0f), c2 = fminf(fmaxf(C3, 0.0f), 1.0f);
+  const float inv = __fdividef(1.0f, c0 + c2);
+  return (c0 * inv) * tau1 + (c2 * inv) * P.tau[2];
 }
 
 }  // namespace lbm

@@ -33,8 +33,59 @@ __device__ __forceinline__ int row_read(int gy, int ny, int periodic) {
 // Mixture density and C of a node of the 3-ring (Eq. 1, 22; reading R1).
 template <int NH>
 __device__ __forceinline__ float node_rho(const DevParams &P, const float (&c)[NH]) {
-  const float C2 = NH == 2 ? c[NH - 1] : 0.0f;
-  return rho_of(P, c[0], C2, 1.0f - c[0] - C2);
+  if constexpr (NH == 1) return rho_of2(P, c[0], 1.0f - c[0]);
+  else return rho_of(P, c[0], c[1], 1.0f - c[0] - c[1]);
+}
+
+// Stencil helpers.  The four direction pairs (a, opp(a)) with a = 1, 2, 5, 6:
+// pair k has direction pair_dir(k).  Sums over e_a are written out so that no
+// product with a zero component of e_a is formed.
+__device__ __host__ constexpr int pair_dir(int k) { return k < 2 ? k + 1 : k + 3; }
+
+// D[k] = v(x + e_a) - v(x - e_a), a = pair_dir(k): twice the central
+// directional derivative along e_a.
+__device__ __forceinline__ void pair_diff(const float (&v)[9], float (&D)[4]) {
+  D[0] = v[1] - v[3];
+  D[1] = v[2] - v[4];
+  D[2] = v[5] - v[7];
+  D[3] = v[6] - v[8];
+}
+
+// Isotropic gradient 3 sum_a w_a e_a v_a from the pair differences
+// (e_5 = (1, 1), e_6 = (-1, 1)).
+__device__ __forceinline__ void iso_grad(const float (&D)[4], float &gx, float &gy) {
+  gx = fmaf(3.0f * LBM_W2, D[2] - D[3], (3.0f * LBM_W1) * D[0]);
+  gy = fmaf(3.0f * LBM_W2, D[2] + D[3], (3.0f * LBM_W1) * D[1]);
+}
+
+// Isotropic Laplacian 6 sum_a w_a (v_a - v_0), from the differences to the
+// centre (exact for neighbouring values close to it).
+__device__ __forceinline__ float iso_lap(const float (&v)[9]) {
+  const float v0 = v[0];
+  const float sa = ((v[1] - v0) + (v[3] - v0)) + ((v[2] - v0) + (v[4] - v0));
+  const float sd = ((v[5] - v0) + (v[7] - v0)) + ((v[6] - v0) + (v[8] - v0));
+  return fmaf(6.0f * LBM_W2, sd, (6.0f * LBM_W1) * sa);
+}
+
+// e_a . (vx, vy) for a != 0.
+__device__ __forceinline__ float edot(int a, float vx, float vy) {
+  const float sx = ex(a) > 0 ? vx : -vx, sy = ey(a) > 0 ? vy : -vy;
+  return ex(a) == 0 ? sy : (ey(a) == 0 ? sx : sx + sy);
+}
+
+// Gamma_a(u) = w_a (1 - 1.5 u.u + 4.5 (e_a.u)^2 + 3 e_a.u) (Eq. 9) of every
+// direction: the even part is shared by opposite directions.
+__device__ __forceinline__ void gamma_all(float ux, float uy, float (&G)[9]) {
+  const float S0 = 1.0f - 1.5f * (ux * ux + uy * uy);
+  G[0] = LBM_W0 * S0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int a = pair_dir(k);
+    const float w = wt(a), eu = edot(a, ux, uy);
+    const float wB = fmaf((4.5f * w) * eu, eu, w * S0);
+    G[a] = fmaf(3.0f * w, eu, wB);
+    G[opp(a)] = fmaf(-3.0f * w, eu, wB);
+  }
 }
 
 // Fields of a node of the 2-ring: moments of g, isotropic gradients of C and
@@ -48,48 +99,44 @@ struct NodeFields {
 template <int NH>
 __device__ __forceinline__ void node_fields(const DevParams &P, const float (&g)[9], const float (&cn)[NH][9],
                                             const float (&rn)[9], NodeFields &f) {
-  float m0 = 0.f, mx = 0.f, my = 0.f;
-#pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    m0 += g[a];
-    mx += ex(a) * g[a];
-    my += ey(a) * g[a];
-  }
+  float Dg[4], Dr[4];
+  pair_diff(g, Dg);
+  const float m0 = (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]))) + g[0];
+  const float mx = Dg[0] + (Dg[2] - Dg[3]);
+  const float my = Dg[1] + (Dg[2] + Dg[3]);
+  pair_diff(rn, Dr);
+  float rx, ry;
+  iso_grad(Dr, rx, ry);
   float C[3], lap[3];
-  float rx = 0.f, ry = 0.f;
-  float cc[3][9];
 #pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    cc[0][a] = cn[0][a];
-    cc[1][a] = NH == 2 ? cn[NH - 1][a] : 0.f;
-    cc[2][a] = 1.0f - cc[0][a] - cc[1][a];
-    rx += wt(a) * ex(a) * rn[a];
-    ry += wt(a) * ey(a) * rn[a];
+  for (int j = 0; j < NH; ++j) {
+    float Dc[4];
+    pair_diff(cn[j], Dc);
+    iso_grad(Dc, f.gCx[j], f.gCy[j]);
+    lap[j] = iso_lap(cn[j]);
+    C[j] = cn[j][0];
   }
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    float sx = 0.f, sy = 0.f, lp = 0.f;
-#pragma unroll
-    for (int a = 1; a < 9; ++a) {
-      sx += wt(a) * ex(a) * cc[j][a];
-      sy += wt(a) * ey(a) * cc[j][a];
-      lp += wt(a) * (cc[j][a] - cc[j][0]);
-    }
-    C[j] = cc[j][0];
-    f.gCx[j] = 3.0f * sx;
-    f.gCy[j] = 3.0f * sy;
-    lap[j] = 6.0f * lp;
+  float Fsx, Fsy;
+  if constexpr (NH == 1) {
+    // C_3 = 1 - C_1 (Eq. 1): its stencils are minus those of C_1
+    C[2] = 1.0f - C[0];
+    f.gCx[2] = -f.gCx[0];
+    f.gCy[2] = -f.gCy[0];
+    lap[2] = -lap[0];
+    f.gCx[1] = f.gCy[1] = f.mu[1] = 0.0f;
+    chem_potentials2(P, C[0], C[2], lap[0], lap[2], f.mu[0], f.mu[2]);
+    Fsx = f.mu[0] * f.gCx[0] + f.mu[2] * f.gCx[2];
+    Fsy = f.mu[0] * f.gCy[0] + f.mu[2] * f.gCy[2];
+  } else {
+    // C_3 = 1 - C_1 - C_2 (Eq. 1): its stencils are minus the sum of the others'
+    C[2] = 1.0f - C[0] - C[1];
+    f.gCx[2] = -(f.gCx[0] + f.gCx[1]);
+    f.gCy[2] = -(f.gCy[0] + f.gCy[1]);
+    lap[2] = -(lap[0] + lap[1]);
+    chem_potentials(P, C, lap, f.mu);
+    Fsx = f.mu[0] * f.gCx[0] + f.mu[1] * f.gCx[1] + f.mu[2] * f.gCx[2];
+    Fsy = f.mu[0] * f.gCy[0] + f.mu[1] * f.gCy[1] + f.mu[2] * f.gCy[2];
   }
-  // C_3 = 1 - C_1 - C_2 (Eq. 1): its stencils are minus the sum of the others'
-  C[2] = cc[2][0];
-  f.gCx[2] = -(f.gCx[0] + f.gCx[1]);
-  f.gCy[2] = -(f.gCy[0] + f.gCy[1]);
-  lap[2] = -(lap[0] + lap[1]);
-  rx *= 3.0f;
-  ry *= 3.0f;
-  chem_potentials(P, C, lap, f.mu);
-  const float Fsx = f.mu[0] * f.gCx[0] + f.mu[1] * f.gCx[1] + f.mu[2] * f.gCx[2];
-  const float Fsy = f.mu[0] * f.gCy[0] + f.mu[1] * f.gCy[1] + f.mu[2] * f.gCy[2];
   const float rho = rn[0];
   const float irho = __fdividef(1.0f, rho);
   f.ux = (3.0f * mx + 0.5f * (Fsx + P.force_x)) * irho;
@@ -115,133 +162,97 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
                                              float (&hs)[NH][9], float (&sv)[NH], float &tn, float &gd2) {
   const float ux = c.ux, uy = c.uy, p = c.p, rho = c.rho;
   const float irho = __fdividef(1.0f, rho);
-  float px = 0.f, py = 0.f, mgx[NH], mgy[NH], mlap[NH];
-#pragma unroll
-  for (int i = 0; i < NH; ++i) mgx[i] = mgy[i] = mlap[i] = 0.f;
-#pragma unroll
-  for (int a = 1; a < 9; ++a) {
-    px += wt(a) * ex(a) * pn[a];
-    py += wt(a) * ey(a) * pn[a];
-#pragma unroll
-    for (int i = 0; i < NH; ++i) {
-      const float m = mun[i][a];
-      mgx[i] += wt(a) * ex(a) * m;
-      mgy[i] += wt(a) * ey(a) * m;
-      mlap[i] += wt(a) * (m - mun[i][0]);
-    }
-  }
-  px *= 3.0f;
-  py *= 3.0f;
-  float Fsx = 0.f, Fsy = 0.f, Cc[NH], kap[NH], udC[NH];
+  // Differences across the node along the direction pairs: the central
+  // directional derivative d_a v = (v(x + e_a) - v(x - e_a)) / 2 is half of
+  // one, and d_opp(a) v = -d_a v.
+  float Dp[4], Dr[4], DC[NH][4];
+  pair_diff(pn, Dp);
+  pair_diff(rn, Dr);
+  float px, py;
+  iso_grad(Dp, px, py);
+  float Fsx, Fsy, Cc[NH], kh[NH], hb[NH], hdmu[NH];
 #pragma unroll
   for (int i = 0; i < NH; ++i) {
+    pair_diff(cn[i], DC[i]);
+    float Dm[4], mgx, mgy;
+    pair_diff(mun[i], Dm);
+    iso_grad(Dm, mgx, mgy);
+    const float lapmu = iso_lap(mun[i]);
     const float gcx = c.gCx[i], gcy = c.gCy[i];
-    Fsx += c.dmu[i] * gcx;
-    Fsy += c.dmu[i] * gcy;
+    Fsx = i == 0 ? c.dmu[0] * gcx : fmaf(c.dmu[i], gcx, Fsx);
+    Fsy = i == 0 ? c.dmu[0] * gcy : fmaf(c.dmu[i], gcy, Fsy);
     Cc[i] = cn[i][0];
     const float D0s = P.d0_sig[i];
-    const float lapmu = 6.0f * mlap[i];
     if (P.mobility == 1)
-      sv[i] = D0s * Cc[i] * (1.0f - Cc[i]) * lapmu +
-              D0s * (1.0f - 2.0f * Cc[i]) * 3.0f * (gcx * mgx[i] + gcy * mgy[i]);
+      sv[i] = D0s * Cc[i] * (1.0f - Cc[i]) * lapmu + D0s * (1.0f - 2.0f * Cc[i]) * (gcx * mgx + gcy * mgy);
     else
       sv[i] = D0s * lapmu;
-    kap[i] = 3.0f * Cc[i] * irho;  // C_i / (rho cs^2)
-    udC[i] = ux * gcx + uy * gcy;
+    kh[i] = 1.5f * Cc[i] * irho;                     // C_i / (rho cs^2) / 2
+    hb[i] = 0.5f * (sv[i] - (ux * gcx + uy * gcy));  // (S_i - u.grad C_i) / 2
+    hdmu[i] = 0.5f * c.dmu[i];
   }
   const float Fby = -rho * P.gravity;
-  const float udr = ux * c.grx + uy * c.gry;
-  const float udFs = ux * Fsx + uy * Fsy;
-  const float udFb = ux * P.force_x + uy * Fby;
+  const float udr3 = (ux * c.grx + uy * c.gry) * kCs2;
+  const float uF = (ux * Fsx + uy * Fsy) + (ux * P.force_x + uy * Fby);
   const float udp = ux * px + uy * py;
-  const float uu = ux * ux + uy * uy;
+  const float S0 = 1.0f - 1.5f * (ux * ux + uy * uy);
   const float rcs2 = rho * kCs2;
-  // central directional derivatives along e_a (x + e_a and x - e_a); those
-  // of opposite directions are negatives of each other
-  float drv[9], dpv[9], dCv[NH][9];
-  drv[0] = dpv[0] = 0.f;
-#pragma unroll
-  for (int i = 0; i < NH; ++i) dCv[i][0] = 0.f;
-#pragma unroll
-  for (int a = 1; a < 9; ++a) {
-    if (a == 1 || a == 2 || a == 5 || a == 6) {
-      drv[a] = 0.5f * (rn[a] - rn[opp(a)]);
-      dpv[a] = 0.5f * (pn[a] - pn[opp(a)]);
-      drv[opp(a)] = -drv[a];
-      dpv[opp(a)] = -dpv[a];
-#pragma unroll
-      for (int i = 0; i < NH; ++i) {
-        dCv[i][a] = 0.5f * (cn[i][a] - cn[i][opp(a)]);
-        dCv[i][opp(a)] = -dCv[i][a];
-      }
-    }
-  }
-  // Per direction a, with Gamma_a = w_a T_a, T_a = 1 - 1.5 u.u + 4.5 (e.u)^2 + 3 e.u:
-  //   E_a   = (e_a - u).(F_s + F_b) = sum_i (mu_i - mu_3) d_a C_i + e_a.F_b - u.F
-  //   ph_a  = (d_a rho - u.grad rho) cs^2 (Gamma_a - w_a) + E_a Gamma_a        (Eq. 14-16)
+  const float c0 = uF - udp;
+  // Per direction a, with Gamma_a = w_a (1 - 1.5 u.u + 4.5 (e.u)^2 + 3 e.u):
+  //   X_a   = sum_i (mu_i - mu_3) d_a C_i + e_a.F_b,   E_a = X_a - u.(F_s + F_b)
+  //   t_a   = (d_a rho - u.grad rho) cs^2
+  //   ph_a  = t_a (Gamma_a - w_a) + E_a Gamma_a                               (Eq. 14-16)
   //   geq_a = w_a p + rho cs^2 (Gamma_a - w_a) - ph_a / 2
-  //   h*_a  = C_i Gamma_a + [d_a C_i - u.grad C_i
-  //            - C_i/(rho cs^2) (d_a p - u.grad p - E_a)] Gamma_a / 2 + S_i Gamma_a / 2   (Eq. 18-20)
-  // e.u, e.F_b and the directional derivatives change sign between opposite
-  // directions, (e.u)^2 does not: those are formed once per pair.
-  const float S0 = 1.0f - 1.5f * uu;
-  const float uF = udFs + udFb;
-  const float udr3 = udr * kCs2;
-  float euv[9], Bv[9], Xv[9];
-  euv[0] = 0.f;
-  Bv[0] = S0;
-  Xv[0] = 0.f;
-#pragma unroll
-  for (int a = 1; a < 9; ++a) {
-    if (a == 1 || a == 2 || a == 5 || a == 6) {
-      const float eu = ex(a) * ux + ey(a) * uy;
-      const float Bp = fmaf(4.5f * eu, eu, S0);
-      float X = ex(a) * P.force_x + ey(a) * Fby;
-#pragma unroll
-      for (int i = 0; i < NH; ++i) X = fmaf(c.dmu[i], dCv[i][a], X);
-      euv[a] = eu;
-      euv[opp(a)] = -eu;
-      Bv[a] = Bv[opp(a)] = Bp;
-      Xv[a] = X;
-      Xv[opp(a)] = -X;
-    }
-  }
-  float eqf[9];
-  float Pxx = 0.f, Pyy = 0.f, Pxy = 0.f;
-#pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    const float exa = (float)ex(a), eya = (float)ey(a), w = wt(a);
-    const float G = w * fmaf(3.0f, euv[a], Bv[a]);
+  //   ep_a  = d_a p - u.grad p - E_a = (d_a p - X_a) + (u.F - u.grad p)
+  //   h*_a  = C_i Gamma_a + Gamma_a [(d_a C_i - u.grad C_i + S_i) / 2
+  //            - C_i / (rho cs^2) ep_a / 2]                                      (Eq. 18-20)
+  // X_a, d_a and e.u change sign between opposite directions, (e.u)^2 does
+  // not: each is formed once per pair.  C_i Gamma_a is kept as its own term so
+  // that the small corrections are not rounded into a value of the size of C_i.
+  float fn[9], eqf[9];
+  auto direction = [&](int a, float G, float E, float t, float ep, const float (&hq)[NH]) {
+    const float w = wt(a);
     const float Gw = G - w;
-    const float E = Xv[a] - uF;
-    const float ph = fmaf(fmaf(drv[a], kCs2, -udr3), Gw, E * G);
+    const float ph = fmaf(t, Gw, E * G);
     const float geq = fmaf(-0.5f, ph, fmaf(rcs2, Gw, w * p));
-    const float fneq = g[a] - geq;
-    g[a] = fneq;
+    fn[a] = g[a] - geq;
     eqf[a] = geq + ph;
-    Pxx += fneq * exa * exa;
-    Pyy += fneq * eya * eya;
-    Pxy += fneq * exa * eya;
-    const float ep = (dpv[a] - udp) - E;
+#pragma unroll
+    for (int i = 0; i < NH; ++i) hs[i][a] = fmaf(Cc[i], G, G * fmaf(-kh[i], ep, hq[i]));
+  };
+  direction(0, LBM_W0 * S0, -uF, -udr3, c0, hb);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int a = pair_dir(k);
+    const float w = wt(a), eu = edot(a, ux, uy);
+    const float wB = fmaf((4.5f * w) * eu, eu, w * S0);
+    float X = edot(a, P.force_x, Fby);
+#pragma unroll
+    for (int i = 0; i < NH; ++i) X = fmaf(hdmu[i], DC[i][k], X);
+    const float o = fmaf(0.5f, Dp[k], -X);
+    float hqa[NH], hqb[NH];
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
-      // C_i Gamma kept as its own term: the small corrections are not rounded
-      // into a value of the size of C_i first
-      const float phh = (dCv[i][a] - udC[i] - kap[i] * ep) * G;
-      hs[i][a] = Cc[i] * G + 0.5f * phh + 0.5f * sv[i] * G;
+      hqa[i] = fmaf(0.25f, DC[i][k], hb[i]);
+      hqb[i] = fmaf(-0.25f, DC[i][k], hb[i]);
     }
+    direction(a, fmaf(3.0f * w, eu, wB), X - uF, fmaf(0.5f * kCs2, Dr[k], -udr3), o + c0, hqa);
+    direction(opp(a), fmaf(-3.0f * w, eu, wB), -X - uF, fmaf(-0.5f * kCs2, Dr[k], -udr3), c0 - o, hqb);
   }
+  // second moments of the non-equilibrium part (pairs 5-7 and 6-8 enter all three)
+  const float s57 = fn[5] + fn[7], s68 = fn[6] + fn[8], sd = s57 + s68;
+  const float Pxx = (fn[1] + fn[3]) + sd, Pyy = (fn[2] + fn[4]) + sd, Pxy = s57 - s68;
   // (1/cs^2) (2 tau / (2 tau + 1)) / (2 tau rho cs^2) = 9 / ((2 tau + 1) rho)
   const float fac = __fdividef(9.0f * irho, 2.0f * tau_prev + 1.0f);
   const float Dxx = -fac * Pxx, Dyy = -fac * Pyy, Dxy = -fac * Pxy;
   // squared strain rate 2 D:D; the power law takes it without a square root
   gd2 = 2.0f * (Dxx * Dxx + Dyy * Dyy + 2.0f * Dxy * Dxy);
-  const float C3 = 1.0f - Cc[0] - (NH == 2 ? Cc[NH - 1] : 0.f);
   const float tau1 = P.powerlaw ? tau_powerlaw_sq(P, gd2, irho) : P.tau[0];
-  tn = tau_mix(P, Cc[0], NH == 2 ? Cc[NH - 1] : 0.f, C3, tau1);
+  if constexpr (NH == 1) tn = tau_mix2(P, Cc[0], 1.0f - Cc[0], tau1);
+  else tn = tau_mix(P, Cc[0], Cc[1], 1.0f - Cc[0] - Cc[1], tau1);
   const float om = __fdividef(1.0f, tn + 0.5f);
 #pragma unroll
-  for (int a = 0; a < 9; ++a) g[a] = (1.0f - om) * g[a] + eqf[a];
+  for (int a = 0; a < 9; ++a) g[a] = (1.0f - om) * fn[a] + eqf[a];
 }
 
 // FP16 deviation codec of the FP16 storage form: g_a is kept as
@@ -329,20 +340,8 @@ __device__ __forceinline__ void store_node(const DevParams &P, const FusedBuffer
     for (int a = 0; a < 9; ++a) B.g_out[(long long)a * plane + ky] = gy[a];
   }
   if constexpr (FORM == 0) {
-    // Gamma_a = w_a (1 - 1.5 u.u + 4.5 (e.u)^2 + 3 e.u): the even part is shared
-    // by opposite directions
-    const float S0 = 1.0f - 1.5f * (ux * ux + uy * uy);
     float G[9];
-    G[0] = wt(0) * S0;
-#pragma unroll
-    for (int a = 1; a < 9; ++a) {
-      if (a == 1 || a == 2 || a == 5 || a == 6) {
-        const float eu = ex(a) * ux + ey(a) * uy;
-        const float Bp = fmaf(4.5f * eu, eu, S0);
-        G[a] = wt(a) * fmaf(3.0f, eu, Bp);
-        G[opp(a)] = wt(a) * fmaf(-3.0f, eu, Bp);
-      }
-    }
+    gamma_all(ux, uy, G);
     float hsv[NH];
 #pragma unroll
     for (int i = 0; i < NH; ++i) hsv[i] = 0.5f * sv[i];
