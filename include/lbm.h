@@ -18,10 +18,15 @@
  * must not be used from two host threads at once.  Host-side inputs and
  * outputs are double precision whatever the device storage.
  *
- * Device data layout (inside the arena): structure of arrays, one plane per
- * population direction, planes of ny rows with a row pitch of nx rounded up to
- * a multiple of 32 floats (128 bytes).  Node (x, y) of plane q is at
- * q * plane + y * pitch + x.
+ * Device data layout (inside the arena): planes of ny rows with a row pitch of
+ * nx rounded up to a multiple of 32 floats (128 bytes), plane stride `plane`.
+ * Fields (tau, C, mu, p, u, ...) are planar: component q of node
+ * k = y * pitch + x is at q * plane + k.  The population arrays (g, and h in
+ * the population state form) interleave their nq planes (9, or 9 (ncomp - 1))
+ * in blocks of 32 columns: direction q of node k is at
+ * ((k / 32) * nq + q) * 32 + k % 32, so that the directions of a node are 128
+ * bytes apart.  The host-side calls (lbm_get_field, lbm_set_fields) use dense
+ * planar doubles whatever the device layout.
  */
 #ifndef LBM_GB300_H
 #define LBM_GB300_H

@@ -53,6 +53,22 @@ static cudaError_t download_planes(lbm_handle *h, const float *src, double *dst,
   return cudaSuccess;
 }
 
+// Copies a device population array (nq planes interleaved in blocks of 32
+// columns, lbm::pop_index) into dense host doubles, plane after plane.
+static cudaError_t download_pops(lbm_handle *h, const float *src, double *dst, int nq) {
+  const int nx = h->prm.nx, ny = h->prm.ny, pitch = h->dp.pitch;
+  const size_t n = (size_t)nq * ny * pitch;
+  h->stage.assign(n, 0.0f);
+  cudaError_t e = cudaMemcpyAsync(h->stage.data(), src, n * sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return e;
+  for (int q = 0; q < nq; ++q)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x)
+        dst[((size_t)q * ny + y) * nx + x] = h->stage[lbm::pop_index((long long)y * pitch + x, q, nq)];
+  return cudaSuccess;
+}
+
 extern "C" {
 
 int lbm_version(void) { return kVersion; }
@@ -315,12 +331,12 @@ lbm_status lbm_get_field(lbm_handle *h, int id, double *out, size_t n) {
   switch (id) {
     case LBM_FIELD_G: {
       const float *g32 = fp32_populations(h, &e);
-      if (e == cudaSuccess) e = download_planes(h, g32, out, 9);
+      if (e == cudaSuccess) e = download_pops(h, g32, out, 9);
       break;
     }
     case LBM_FIELD_H:
       if (h->prm.collapse_h) return h->fail(LBM_E_STATE, "the collapsed state form stores no h populations");
-      e = download_planes(h, h->h[h->cur], out, 9 * nh);
+      e = download_pops(h, h->h[h->cur], out, 9 * nh);
       break;
     case LBM_FIELD_TAU: e = download_planes(h, h->tau[h->cur], out, 1); break;
     case LBM_FIELD_SHEAR: e = download_planes(h, h->shear, out, 1); break;

@@ -65,8 +65,9 @@ __device__ __forceinline__ int i1(int lx, int ly) { return (ly + 1) * (TX + 2) +
 // FORM 2: as FORM 1, and g is stored as FP16 deviations from a per-node
 // reference: d_a = (g_a - w_a P) * scale with P = sum_a g_a kept in FP32 (the
 // pressure-sized part stays in FP32, only the small deviations go to FP16),
-// 60 bytes per node-step.  In memory: 9 half planes, then the FP32 P plane,
-// inside the space of the 9 FP32 planes.
+// 60 bytes per node-step.  In memory: 9 half planes interleaved in blocks of
+// 32 columns (pop_index), then the planar FP32 P plane, inside the space of the
+// 9 FP32 planes.
 // NT threads per CTA (NT >= TX * TY); NT close to the size of R1 lets the
 // heaviest stage run in one pass.
 template <int TX, int TY, int NH, int FORM, int NT>
@@ -404,12 +405,12 @@ __global__ void k_g16_encode(DevParams P, const float *__restrict__ g32, float *
   if (k >= P.plane) return;
   float g[9];
 #pragma unroll
-  for (int a = 0; a < 9; ++a) g[a] = g32[a * P.plane + k];
+  for (int a = 0; a < 9; ++a) g[a] = g32[pop_index(k, a, 9)];
   const float Pn = g16_reference(g);
   g16[(9 * P.plane) / 2 + k] = Pn;
   __half *gh = reinterpret_cast<__half *>(g16);
 #pragma unroll
-  for (int a = 0; a < 9; ++a) gh[a * P.plane + k] = g16_encode(g[a], Pn, a, P.g16_scale);
+  for (int a = 0; a < 9; ++a) gh[pop_index(k, a, 9)] = g16_encode(g[a], Pn, a, P.g16_scale);
 }
 
 __global__ void k_g16_decode(DevParams P, const float *__restrict__ g16, float *__restrict__ g32) {
@@ -418,7 +419,7 @@ __global__ void k_g16_decode(DevParams P, const float *__restrict__ g16, float *
   const float Pref = g16[(9 * P.plane) / 2 + k];
   const __half *gh = reinterpret_cast<const __half *>(g16);
 #pragma unroll
-  for (int a = 0; a < 9; ++a) g32[a * P.plane + k] = g16_decode(Pref, gh[a * P.plane + k], a, P.g16_inv_scale);
+  for (int a = 0; a < 9; ++a) g32[pop_index(k, a, 9)] = g16_decode(Pref, gh[pop_index(k, a, 9)], a, P.g16_inv_scale);
 }
 
 cudaError_t launch_g16_encode(const DevParams &P, const float *g32, float *g16, cudaStream_t s) {

@@ -17,7 +17,9 @@ namespace lbm_detail {
 
 constexpr int kVersion = 100;  // 0.1.0
 constexpr size_t kAlign = 256;
-inline constexpr char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '0'};
+// checkpoint magic; the last character names the population layout (2: planes
+// interleaved in blocks of 32 columns)
+inline constexpr char kMagic[8] = {'L', 'B', 'M', 'G', 'B', '3', '0', '2'};
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 

@@ -7,6 +7,17 @@
 
 namespace lbm {
 
+// Population arrays (g, and h in the population state form) keep their nq
+// planes interleaved in blocks of 32 columns: element q of node
+// k = y * pitch + x (pitch a multiple of 32) is at
+// ((k / 32) * nq + q) * 32 + k % 32, so the planes of a node are 128 bytes
+// apart, a constant the step kernels fold into their loads and stores.  Every
+// other array (tau, C, mu, p, u, ...) is planar: element i of node k at
+// i * plane + k.
+__host__ __device__ constexpr long long pop_index(long long k, int q, int nq) {
+  return ((k >> 5) * nq + q) * 32 + (k & 31);
+}
+
 // Device buffers of one step.  *_in are the current state, *_out the next one;
 // the remaining planes are scratch fields.
 struct StepBuffers {

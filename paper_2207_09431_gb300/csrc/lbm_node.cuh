@@ -282,9 +282,10 @@ __device__ __forceinline__ void load_order_parameters(const FusedBuffers &B, lon
   for (int i = 0; i < NH; ++i) {
     float acc;
     if constexpr (FORM == 0) {
+      const float *hp = B.h_in + pop_index(k, i * 9, 9 * NH);
       acc = 0.f;
 #pragma unroll
-      for (int a = 0; a < 9; ++a) acc += B.h_in[((long long)i * 9 + a) * plane + k];
+      for (int a = 0; a < 9; ++a) acc += hp[a * 32];
     } else {
       acc = B.h_in[(long long)i * plane + k];
     }
@@ -298,12 +299,13 @@ __device__ __forceinline__ void load_populations(const DevParams &P, const Fused
                                                  long long k, float (&g)[9]) {
   if constexpr (FORM == 2) {
     const float Pref = B.g_in[(9 * plane) / 2 + k];
-    const __half *gh = reinterpret_cast<const __half *>(B.g_in);
+    const __half *gh = reinterpret_cast<const __half *>(B.g_in) + pop_index(k, 0, 9);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) g[a] = g16_decode(Pref, gh[(long long)a * plane + k], a, P.g16_inv_scale);
+    for (int a = 0; a < 9; ++a) g[a] = g16_decode(Pref, gh[a * 32], a, P.g16_inv_scale);
   } else {
+    const float *gp = B.g_in + pop_index(k, 0, 9);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) g[a] = B.g_in[(long long)a * plane + k];
+    for (int a = 0; a < 9; ++a) g[a] = gp[a * 32];
   }
 }
 
@@ -332,12 +334,13 @@ __device__ __forceinline__ void store_node(const DevParams &P, const FusedBuffer
   if constexpr (FORM == 2) {
     const float Pn = g16_reference(gy);
     B.g_out[(9 * plane) / 2 + ky] = Pn;
-    __half *gh = reinterpret_cast<__half *>(B.g_out);
+    __half *gh = reinterpret_cast<__half *>(B.g_out) + pop_index(ky, 0, 9);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) gh[(long long)a * plane + ky] = g16_encode(gy[a], Pn, a, P.g16_scale);
+    for (int a = 0; a < 9; ++a) gh[a * 32] = g16_encode(gy[a], Pn, a, P.g16_scale);
   } else {
+    float *go = B.g_out + pop_index(ky, 0, 9);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) B.g_out[(long long)a * plane + ky] = gy[a];
+    for (int a = 0; a < 9; ++a) go[a * 32] = gy[a];
   }
   if constexpr (FORM == 0) {
     float G[9];
@@ -345,10 +348,11 @@ __device__ __forceinline__ void store_node(const DevParams &P, const FusedBuffer
     float hsv[NH];
 #pragma unroll
     for (int i = 0; i < NH; ++i) hsv[i] = 0.5f * sv[i];
+    float *ho = B.h_out + pop_index(ky, 0, 9 * NH);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
 #pragma unroll
-      for (int i = 0; i < NH; ++i) B.h_out[((long long)i * 9 + a) * plane + ky] = fmaf(hsv[i], G[a], hy[i][a]);
+      for (int i = 0; i < NH; ++i) ho[(i * 9 + a) * 32] = fmaf(hsv[i], G[a], hy[i][a]);
     }
   } else {
 #pragma unroll

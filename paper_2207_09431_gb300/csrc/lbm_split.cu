@@ -142,7 +142,7 @@ __global__ void k_moments(DevParams P, const float *__restrict__ h, float *__res
   const long long k = node_index(P, x, y);
   for (int i = 0; i < P.nh; ++i) {
     float s = 0.f;
-    for (int a = 0; a < 9; ++a) s += h[((long long)i * 9 + a) * P.plane + k];
+    for (int a = 0; a < 9; ++a) s += h[pop_index(k, i * 9 + a, 9 * P.nh)];
     C[(long long)i * P.plane + k] = s;
   }
 }
@@ -193,7 +193,7 @@ __global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float 
   n.Fb[1] = -n.rho * P.gravity;
   float ga[9], m0 = 0.f, mx = 0.f, my = 0.f;
   for (int a = 0; a < 9; ++a) {
-    ga[a] = g[(long long)a * P.plane + k];
+    ga[a] = g[pop_index(k, a, 9)];
     m0 += ga[a];
     mx += ex(a) * ga[a];
     my += ey(a) * ga[a];
@@ -300,7 +300,7 @@ __global__ void k_collide(DevParams P, const float *__restrict__ g, const float 
     const float G = gamma_a(a, n.ux, n.uy);
     const float pg = phi_g(n, a, G);
     const float geq = wt(a) * n.p + n.rho * kCs2 * (G - wt(a)) - 0.5f * pg;
-    const float gv = g[(long long)a * P.plane + k];
+    const float gv = g[pop_index(k, a, 9)];
     const float gstar = gv - omega * (gv - geq) + pg;
     // destination
     int dx = x + ex(a), dy = y + ey(a);
@@ -314,12 +314,12 @@ __global__ void k_collide(DevParams P, const float *__restrict__ g, const float 
     } else {
       kd = node_index(P, wrap_x(dx, P.nx), P.periodic_y ? wrap_y(dy, P.ny, 1) : dy);
     }
-    g_out[(long long)da * P.plane + kd] = gstar;
+    g_out[pop_index(kd, da, 9)] = gstar;
     const float Gd = gamma_a(da, uxf[kd], uyf[kd]);
     for (int i = 0; i < P.nh; ++i) {
       const float ph = phi_h(n, i, a, G);
       const float hstar = n.C[i] * G + 0.5f * ph + 0.5f * sv[i] * G;
-      h_out[((long long)i * 9 + da) * P.plane + kd] = hstar + 0.5f * SV[(long long)i * P.plane + kd] * Gd;
+      h_out[pop_index(kd, i * 9 + da, 9 * P.nh)] = hstar + 0.5f * SV[(long long)i * P.plane + kd] * Gd;
     }
   }
 }
@@ -357,11 +357,11 @@ __global__ void k_open_x(DevParams P, const float *__restrict__ g_old, const flo
       const float w = wt(a);
       const float eq_in = w * p + rho * kCs2 * (gamma_a(a, P.u_in, 0.0f) - w);
       const float eq_0 = w * p + rho * kCs2 * (gamma_a(a, uxf[k0], uyf[k0]) - w);
-      g_out[(long long)a * pl + k] = eq_in + (g_out[(long long)a * pl + k1] - eq_0);
+      g_out[pop_index(k, a, 9)] = eq_in + (g_out[pop_index(k1, a, 9)] - eq_0);
       const float G = gamma_a(a, uxf[k], uyf[k]);
       const float Gin = gamma_a(a, P.u_in, 0.0f);
       for (int i = 0; i < P.nh; ++i)
-        h_out[((long long)i * 9 + a) * pl + k] = P.c_in[i] * Gin + 0.5f * SV[(long long)i * pl + k] * G;
+        h_out[pop_index(k, i * 9 + a, 9 * P.nh)] = P.c_in[i] * Gin + 0.5f * SV[(long long)i * pl + k] * G;
     }
   }
   // outlet
@@ -378,17 +378,17 @@ __global__ void k_open_x(DevParams P, const float *__restrict__ g_old, const flo
       if (!P.periodic_y && (sy < 0 || sy >= P.ny)) continue;
       set[a] = true;
       wsum += wt(a);
-      g_out[(long long)a * pl + k] = (g_old[(long long)a * pl + k] + U * g_out[(long long)a * pl + kin]) * inv;
+      g_out[pop_index(k, a, 9)] = (g_old[pop_index(k, a, 9)] + U * g_out[pop_index(kin, a, 9)]) * inv;
       for (int i = 0; i < P.nh; ++i) {
-        const long long ia = ((long long)i * 9 + a) * pl;
-        h_out[ia + k] = (h_old[ia + k] + U * h_out[ia + kin]) * inv;
+        const int q = i * 9 + a, nq = 9 * P.nh;
+        h_out[pop_index(k, q, nq)] = (h_old[pop_index(k, q, nq)] + U * h_out[pop_index(kin, q, nq)]) * inv;
       }
     }
     if (wsum > 0.f) {
       float p0 = 0.f;
-      for (int a = 0; a < 9; ++a) p0 += g_out[(long long)a * pl + k];
+      for (int a = 0; a < 9; ++a) p0 += g_out[pop_index(k, a, 9)];
       for (int a = 0; a < 9; ++a)
-        if (set[a]) g_out[(long long)a * pl + k] -= p0 * wt(a) / wsum;
+        if (set[a]) g_out[pop_index(k, a, 9)] -= p0 * wt(a) / wsum;
     }
   }
 }
@@ -420,10 +420,10 @@ __global__ void k_init(DevParams P, const float *__restrict__ Cf, const float *_
   n.Fb[1] = -n.rho * P.gravity;
   for (int a = 0; a < 9; ++a) {
     const float G = gamma_a(a, n.ux, n.uy);
-    g[(long long)a * P.plane + k] = wt(a) * n.p + n.rho * kCs2 * (G - wt(a)) - 0.5f * phi_g(n, a, G);
+    g[pop_index(k, a, 9)] = wt(a) * n.p + n.rho * kCs2 * (G - wt(a)) - 0.5f * phi_g(n, a, G);
     if (h)
       for (int i = 0; i < P.nh; ++i)
-        h[((long long)i * 9 + a) * P.plane + k] = n.C[i] * G - 0.5f * phi_h(n, i, a, G);
+        h[pop_index(k, i * 9 + a, 9 * P.nh)] = n.C[i] * G - 0.5f * phi_h(n, i, a, G);
   }
   const float tau1 = P.powerlaw ? tau_powerlaw(P, 0.0f, 1.0f / n.rho) : P.tau[0];
   tau[k] = tau_mix(P, n.C[0], n.C[1], n.C[2], tau1);

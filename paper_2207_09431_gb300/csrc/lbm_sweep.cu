@@ -153,19 +153,26 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
     item_rows(j, r0, r1, r2, a0, a1, a2);
     if (a0) {
       const long long k0 = (long long)row_read(r0, ny, per) * pitch + x0c;
+      if constexpr (FORM == 0) {
+        const float *hp = B.h_in + pop_index(k0, 0, NS0);
 #pragma unroll
-      for (int q = 0; q < NS0; ++q) nh[q] = B.h_in[(long long)q * plane + k0];
+        for (int q = 0; q < NS0; ++q) nh[q] = hp[q * 32];
+      } else {
+#pragma unroll
+        for (int q = 0; q < NS0; ++q) nh[q] = B.h_in[(long long)q * plane + k0];
+      }
     }
     if (a1) {
       const long long k1 = (long long)(per ? wrap_periodic(r1, ny) : r1) * pitch + x1c;
       if constexpr (FORM == 2) {
-        const __half *gh = reinterpret_cast<const __half *>(B.g_in);
+        const __half *gh = reinterpret_cast<const __half *>(B.g_in) + pop_index(k1, 0, 9);
         nP = B.g_in[(9 * plane) / 2 + k1];
 #pragma unroll
-        for (int a = 0; a < 9; ++a) ngh[a] = gh[(long long)a * plane + k1];
+        for (int a = 0; a < 9; ++a) ngh[a] = gh[a * 32];
       } else {
+        const float *gp = B.g_in + pop_index(k1, 0, 9);
 #pragma unroll
-        for (int a = 0; a < 9; ++a) ng[a] = B.g_in[(long long)a * plane + k1];
+        for (int a = 0; a < 9; ++a) ng[a] = gp[a * 32];
       }
     }
     if (a2) nt = B.tau_in[(long long)(per ? wrap_periodic(r2, ny) : r2) * pitch + x2c];
