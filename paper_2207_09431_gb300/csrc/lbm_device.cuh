@@ -93,13 +93,15 @@ __device__ __forceinline__ void chem_potentials(const DevParams &P, const float 
   mu[2] = P.mu_pre * ((d2 - d0) * P.inv_sig[0] + (d2 - d1) * P.inv_sig[1]) - P.grad_coef[2] * lapC[2];
 }
 
-// Two-component forms (C_2 = 0 identically): the same values as rho_of,
-// chem_potentials and tau_mix with C_2 = 0, without the terms that vanish
-// with C_2 (products with a constant zero are kept by IEEE arithmetic).
-__device__ __forceinline__ float rho_of2(const DevParams &P, float C1, float C3) {
-  const float c0 = fminf(fmaxf(C1, 0.0f), 1.0f), c2 = fminf(fmaxf(C3, 0.0f), 1.0f);
-  const float inv = __fdividef(1.0f, c0 + c2);
-  return (c0 * inv) * P.rho[0] + (c2 * inv) * P.rho[2];
+// Two-component forms (C_2 = 0 identically, C_3 = 1 - C_1): the same values
+// as rho_of, chem_potentials and tau_mix with C_2 = 0, without the terms that
+// vanish with C_2 (products with a constant zero are kept by IEEE
+// arithmetic).  The clipped weights of R1 then sum to one exactly
+// (clip(C_1) + clip(1 - C_1) = 1 for every C_1), so their normalisation is
+// the identity and is left out.
+__device__ __forceinline__ float rho_of2(const DevParams &P, float C1) {
+  const float c0 = fminf(fmaxf(C1, 0.0f), 1.0f), c2 = fminf(fmaxf(1.0f - C1, 0.0f), 1.0f);
+  return c0 * P.rho[0] + c2 * P.rho[2];
 }
 
 // mu_1 and mu_3 of Eq. 5 with C_2 = 0: dE0/dC_1 = 2 Sigma_13 C_1 C_3^2,
@@ -145,10 +147,9 @@ __device__ __forceinline__ float tau_mix(const DevParams &P, float C1, float C2,
   return c[0] * tau1 + c[1] * P.tau[1] + c[2] * P.tau[2];
 }
 
-__device__ __forceinline__ float tau_mix2(const DevParams &P, float C1, float C3, float tau1) {
-  const float c0 = fminf(fmaxf(C1, 0.0f), 1.0f), c2 = fminf(fmaxf(C3, 0.0f), 1.0f);
-  const float inv = __fdividef(1.0f, c0 + c2);
-  return (c0 * inv) * tau1 + (c2 * inv) * P.tau[2];
+__device__ __forceinline__ float tau_mix2(const DevParams &P, float C1, float tau1) {
+  const float c0 = fminf(fmaxf(C1, 0.0f), 1.0f), c2 = fminf(fmaxf(1.0f - C1, 0.0f), 1.0f);
+  return c0 * tau1 + c2 * P.tau[2];
 }
 
 }  // namespace lbm

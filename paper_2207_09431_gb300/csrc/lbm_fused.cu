@@ -166,16 +166,20 @@ __device__ __forceinline__ void fused_tile(const DevParams &P, const FusedBuffer
     c.uy = s.uy[c2];
     c.p = pn[0];
     c.rho = rn[0];
+    c.irho = __fdividef(1.0f, rn[0]);
     c.grx = s.grx[c2];
     c.gry = s.gry[c2];
+    pair_diff(rn, c.Dr);
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
       c.dmu[i] = s.dmu[i][c2];
       c.gCx[i] = s.gCx[i][c2];
       c.gCy[i] = s.gCy[i][c2];
+      c.C[i] = cn[i][0];
+      pair_diff(cn[i], c.DC[i]);
     }
     float hs[NH][9], sv[NH], tn, gd2;
-    node_collide<NH>(P, c, pn, rn, cn, mun, g, B.tau_in[k], hs, sv, tn, gd2);
+    node_collide<NH>(P, c, pn, mun, g, B.tau_in[k], hs, sv, tn, gd2);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       s.g[a][c2] = g[a];

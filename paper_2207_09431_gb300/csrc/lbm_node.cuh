@@ -33,7 +33,7 @@ __device__ __forceinline__ int row_read(int gy, int ny, int periodic) {
 // Mixture density and C of a node of the 3-ring (Eq. 1, 22; reading R1).
 template <int NH>
 __device__ __forceinline__ float node_rho(const DevParams &P, const float (&c)[NH]) {
-  if constexpr (NH == 1) return rho_of2(P, c[0], 1.0f - c[0]);
+  if constexpr (NH == 1) return rho_of2(P, c[0]);
   else return rho_of(P, c[0], c[1], 1.0f - c[0] - c[1]);
 }
 
@@ -93,28 +93,28 @@ __device__ __forceinline__ void gamma_all(float ux, float uy, float (&G)[9]) {
 // reading R3).
 struct NodeFields {
   float mu[3], gCx[3], gCy[3];
-  float rx, ry, ux, uy, p;
+  float rx, ry, ux, uy, p, rho, irho;
+  float C[2], Dr[4], DC[2][4];  // C_i, and the pair differences of rho and C_i
 };
 
 template <int NH>
 __device__ __forceinline__ void node_fields(const DevParams &P, const float (&g)[9], const float (&cn)[NH][9],
                                             const float (&rn)[9], NodeFields &f) {
-  float Dg[4], Dr[4];
+  float Dg[4];
   pair_diff(g, Dg);
   const float m0 = (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8]))) + g[0];
   const float mx = Dg[0] + (Dg[2] - Dg[3]);
   const float my = Dg[1] + (Dg[2] + Dg[3]);
-  pair_diff(rn, Dr);
+  pair_diff(rn, f.Dr);
   float rx, ry;
-  iso_grad(Dr, rx, ry);
+  iso_grad(f.Dr, rx, ry);
   float C[3], lap[3];
 #pragma unroll
   for (int j = 0; j < NH; ++j) {
-    float Dc[4];
-    pair_diff(cn[j], Dc);
-    iso_grad(Dc, f.gCx[j], f.gCy[j]);
+    pair_diff(cn[j], f.DC[j]);
+    iso_grad(f.DC[j], f.gCx[j], f.gCy[j]);
     lap[j] = iso_lap(cn[j]);
-    C[j] = cn[j][0];
+    C[j] = f.C[j] = cn[j][0];
   }
   float Fsx, Fsy;
   if constexpr (NH == 1) {
@@ -139,6 +139,8 @@ __device__ __forceinline__ void node_fields(const DevParams &P, const float (&g)
   }
   const float rho = rn[0];
   const float irho = __fdividef(1.0f, rho);
+  f.rho = rho;
+  f.irho = irho;
   f.ux = (3.0f * mx + 0.5f * (Fsx + P.force_x)) * irho;
   f.uy = (3.0f * my + 0.5f * (Fsy - rho * P.gravity)) * irho;
   f.p = m0 + 0.5f * kCs2 * (f.ux * rx + f.uy * ry);
@@ -150,30 +152,31 @@ __device__ __forceinline__ void node_fields(const DevParams &P, const float (&g)
 // R8), h* of every direction (Eq. 18, tau_h = 1/2), strain rate from the
 // non-equilibrium part with the previous tau (Eq. 25-29, reading R23), the new
 // tau (Eq. 31-33, R4) and g* of every direction (Eq. 14).
+// The node's own values come from the field stage (NodeFields of the same
+// node): rho and 1 / rho, C_i, and the pair differences of rho and C_i.
 struct NodeCenter {
-  float ux, uy, p, rho, grx, gry;
+  float ux, uy, p, rho, irho, grx, gry;
   float dmu[2], gCx[2], gCy[2];
+  float C[2], Dr[4], DC[2][4];
 };
 
 template <int NH>
 __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCenter &c, const float (&pn)[9],
-                                             const float (&rn)[9], const float (&cn)[NH][9],
                                              const float (&mun)[NH][9], float (&g)[9], float tau_prev,
                                              float (&hs)[NH][9], float (&sv)[NH], float &tn, float &gd2) {
   const float ux = c.ux, uy = c.uy, p = c.p, rho = c.rho;
-  const float irho = __fdividef(1.0f, rho);
+  const float irho = c.irho;
   // Differences across the node along the direction pairs: the central
   // directional derivative d_a v = (v(x + e_a) - v(x - e_a)) / 2 is half of
   // one, and d_opp(a) v = -d_a v.
-  float Dp[4], Dr[4], DC[NH][4];
+  float Dp[4];
   pair_diff(pn, Dp);
-  pair_diff(rn, Dr);
+  const float (&Dr)[4] = c.Dr;
   float px, py;
   iso_grad(Dp, px, py);
   float Fsx, Fsy, Cc[NH], kh[NH], hb[NH], hdmu[NH];
 #pragma unroll
   for (int i = 0; i < NH; ++i) {
-    pair_diff(cn[i], DC[i]);
     float Dm[4], mgx, mgy;
     pair_diff(mun[i], Dm);
     iso_grad(Dm, mgx, mgy);
@@ -181,7 +184,7 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
     const float gcx = c.gCx[i], gcy = c.gCy[i];
     Fsx = i == 0 ? c.dmu[0] * gcx : fmaf(c.dmu[i], gcx, Fsx);
     Fsy = i == 0 ? c.dmu[0] * gcy : fmaf(c.dmu[i], gcy, Fsy);
-    Cc[i] = cn[i][0];
+    Cc[i] = c.C[i];
     const float D0s = P.d0_sig[i];
     if (P.mobility == 1)
       sv[i] = D0s * Cc[i] * (1.0f - Cc[i]) * lapmu + D0s * (1.0f - 2.0f * Cc[i]) * (gcx * mgx + gcy * mgy);
@@ -228,13 +231,13 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
     const float wB = fmaf((4.5f * w) * eu, eu, w * S0);
     float X = edot(a, P.force_x, Fby);
 #pragma unroll
-    for (int i = 0; i < NH; ++i) X = fmaf(hdmu[i], DC[i][k], X);
+    for (int i = 0; i < NH; ++i) X = fmaf(hdmu[i], c.DC[i][k], X);
     const float o = fmaf(0.5f, Dp[k], -X);
     float hqa[NH], hqb[NH];
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
-      hqa[i] = fmaf(0.25f, DC[i][k], hb[i]);
-      hqb[i] = fmaf(-0.25f, DC[i][k], hb[i]);
+      hqa[i] = fmaf(0.25f, c.DC[i][k], hb[i]);
+      hqb[i] = fmaf(-0.25f, c.DC[i][k], hb[i]);
     }
     direction(a, fmaf(3.0f * w, eu, wB), X - uF, fmaf(0.5f * kCs2, Dr[k], -udr3), o + c0, hqa);
     direction(opp(a), fmaf(-3.0f * w, eu, wB), -X - uF, fmaf(-0.5f * kCs2, Dr[k], -udr3), c0 - o, hqb);
@@ -248,7 +251,7 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
   // squared strain rate 2 D:D; the power law takes it without a square root
   gd2 = 2.0f * (Dxx * Dxx + Dyy * Dyy + 2.0f * Dxy * Dxy);
   const float tau1 = P.powerlaw ? tau_powerlaw_sq(P, gd2, irho) : P.tau[0];
-  if constexpr (NH == 1) tn = tau_mix2(P, Cc[0], 1.0f - Cc[0], tau1);
+  if constexpr (NH == 1) tn = tau_mix2(P, Cc[0], tau1);
   else tn = tau_mix(P, Cc[0], Cc[1], 1.0f - Cc[0] - Cc[1], tau1);
   const float om = __fdividef(1.0f, tn + 0.5f);
 #pragma unroll

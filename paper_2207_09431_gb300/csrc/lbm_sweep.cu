@@ -56,16 +56,22 @@ struct PairVec<2> {
   static __device__ __forceinline__ float last(const T &v) { return v.z; }
 };
 
-template <int TX, int RS, int NH>
+// REC: the collision's own C_i, rho, 1 / rho and the pair differences of rho
+// and C_i travel from stage 1 in the record, and stage 2 reads no (C, rho)
+// ring.  Used by the C state forms; the population form reads them again from
+// the ring, because the larger record would push the shared memory of three
+// CTAs past the carveout that leaves its (larger) loads in flight enough L1.
+template <int TX, int RS, int NH, bool REC>
 struct PipeSmem {
   using PV = PairVec<NH>;
   using V = typename PV::T;
   static constexpr int W3 = TX + 6, W2 = TX + 4, W1 = TX + 2;
   // ring depths: rows alive at once (written this step or read this step)
-  static constexpr int D3 = 3 * RS + 3, D2 = 2 * RS + 2, DA = 2 * RS + 1, DB = 2 * RS + 2;
+  static constexpr int D3 = REC ? 2 * RS + 2 : 3 * RS + 3, D2 = 2 * RS + 2, DA = 2 * RS + 1, DB = 2 * RS + 2;
   // stage 1 -> stage 2 record of a 1-ring node, in float4 words: g_0..g_8,
-  // u_x, u_y, grad rho, then mu_i - mu_3, d_x C_i, d_y C_i per component
-  static constexpr int NR = 13 + 3 * NH, NQ = (NR + 3) / 4;
+  // u_x, u_y, grad rho, then mu_i - mu_3, d_x C_i, d_y C_i per component, and
+  // (REC) C_i, rho, 1 / rho and the pair differences of rho and of each C_i
+  static constexpr int NR = REC ? 19 + 8 * NH : 13 + 3 * NH, NQ = (NR + 3) / 4;
   float4 da[NQ][DA][W1];
   V cr[D3][W3];  // (C_i, rho) of the 3-ring
   V mp[D2][W2];  // (mu_i, p) of the 2-ring
@@ -96,8 +102,9 @@ __device__ __forceinline__ int row_slot(int dy, int sdn, int s, int sup) { retur
 // in y, 1 periodic y, 2 taken from P at run time (batches mix both).
 template <int TX, int RS, int NH, int FORM, int PER, int NT>
 __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffers &B, int x0, int ys, int ye,
-                                           PipeSmem<TX, RS, NH> &s) {
-  using S = PipeSmem<TX, RS, NH>;
+                                           PipeSmem<TX, RS, NH, FORM != 0> &s) {
+  constexpr bool REC = FORM != 0;
+  using S = PipeSmem<TX, RS, NH, REC>;
   using PV = typename S::PV;
   using V = typename S::V;
   static_assert(NT >= RS * S::W3, "one item of every stage per thread");
@@ -239,6 +246,18 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
           rec[13 + NH + q] = f.gCx[q];
           rec[13 + 2 * NH + q] = f.gCy[q];
         }
+        if constexpr (REC) {
+#pragma unroll
+          for (int q = 0; q < NH; ++q) rec[13 + 3 * NH + q] = f.C[q];
+          rec[13 + 4 * NH] = f.rho;
+          rec[14 + 4 * NH] = f.irho;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            rec[15 + 4 * NH + k] = f.Dr[k];
+#pragma unroll
+            for (int q = 0; q < NH; ++q) rec[19 + 4 * NH + 4 * q + k] = f.DC[q][k];
+          }
+        }
 #pragma unroll
         for (int k = S::NR; k < 4 * S::NQ; ++k) rec[k] = 0.f;
 #pragma unroll
@@ -292,18 +311,13 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
         if (r2 == 0) mdn = s2m;
         if (r2 == ny - 1) mup = s2m;
       }
-      float pn[9], rn[9], cn[NH][9], mun[NH][9], g2[9];
+      float pn[9], mun[NH][9], g2[9];
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        const V cr = s.cr[row_slot(ey(a), cdn, s2c, cup)][c2 + 2 + ex(a)];
         const V mp = s.mp[row_slot(ey(a), mdn, s2m, mup)][c2 + 1 + ex(a)];
         pn[a] = PV::last(mp);
-        rn[a] = PV::last(cr);
 #pragma unroll
-        for (int q = 0; q < NH; ++q) {
-          cn[q][a] = PV::comp(cr, q);
-          mun[q][a] = PV::comp(mp, q);
-        }
+        for (int q = 0; q < NH; ++q) mun[q][a] = PV::comp(mp, q);
       }
       float rec[4 * S::NQ];
 #pragma unroll
@@ -322,15 +336,44 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
       nc.grx = rec[11];
       nc.gry = rec[12];
       nc.p = pn[0];
-      nc.rho = rn[0];
 #pragma unroll
       for (int q = 0; q < NH; ++q) {
         nc.dmu[q] = rec[13 + q];
         nc.gCx[q] = rec[13 + NH + q];
         nc.gCy[q] = rec[13 + 2 * NH + q];
       }
+      if constexpr (REC) {
+#pragma unroll
+        for (int q = 0; q < NH; ++q) nc.C[q] = rec[13 + 3 * NH + q];
+        nc.rho = rec[13 + 4 * NH];
+        nc.irho = rec[14 + 4 * NH];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          nc.Dr[k] = rec[15 + 4 * NH + k];
+#pragma unroll
+          for (int q = 0; q < NH; ++q) nc.DC[q][k] = rec[19 + 4 * NH + 4 * q + k];
+        }
+      } else {
+        // C and rho of the 3x3 stencil from the ring
+        float rn[9], cn[NH][9];
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+          const V cr = s.cr[row_slot(ey(a), cdn, s2c, cup)][c2 + 2 + ex(a)];
+          rn[a] = PV::last(cr);
+#pragma unroll
+          for (int q = 0; q < NH; ++q) cn[q][a] = PV::comp(cr, q);
+        }
+        nc.rho = rn[0];
+        nc.irho = __fdividef(1.0f, rn[0]);
+        pair_diff(rn, nc.Dr);
+#pragma unroll
+        for (int q = 0; q < NH; ++q) {
+          nc.C[q] = cn[q][0];
+          pair_diff(cn[q], nc.DC[q]);
+        }
+      }
       float hs[NH][9], sv[NH], tn, gd2;
-      node_collide<NH>(P, nc, pn, rn, cn, mun, g2, tprev, hs, sv, tn, gd2);
+      node_collide<NH>(P, nc, pn, mun, g2, tprev, hs, sv, tn, gd2);
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         s.gs[a][s2b][c2] = g2[a];
@@ -361,7 +404,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffe
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ys = blockIdx.y * seg_len;
   sweep_body<TX, RS, NH, FORM, PER, NT>(P, B, blockIdx.x * TX, ys, min(ys + seg_len, P.ny),
-                                        *reinterpret_cast<PipeSmem<TX, RS, NH> *>(smem_raw));
+                                        *reinterpret_cast<PipeSmem<TX, RS, NH, FORM != 0> *>(smem_raw));
 }
 
 // Many lattices in one launch: CTA b sweeps work item b = (case, strip origin,
@@ -379,7 +422,8 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep_batched(const BatchCase *__r
     sB = cases[w.case_id].B[cases[w.case_id].base_parity ^ parity];
   }
   __syncthreads();
-  sweep_body<TX, RS, NH, FORM, 2, NT>(sP, sB, w.x0, w.y0, w.y1, *reinterpret_cast<PipeSmem<TX, RS, NH> *>(smem_raw));
+  sweep_body<TX, RS, NH, FORM, 2, NT>(sP, sB, w.x0, w.y0, w.y1,
+                                      *reinterpret_cast<PipeSmem<TX, RS, NH, FORM != 0> *>(smem_raw));
 }
 
 // Segment length for a strip count: balances the waves of CTAs against the
@@ -405,7 +449,7 @@ int choose_segment(int ny, int strips, int resident, int rs) {
 
 template <int TX, int RS, int NH, int FORM, int PER, int NT, int MINB>
 cudaError_t launch_sweep_per(const DevParams &P, const FusedBuffers &B, cudaStream_t st) {
-  const size_t smem = sizeof(PipeSmem<TX, RS, NH>);
+  const size_t smem = sizeof(PipeSmem<TX, RS, NH, FORM != 0>);
   static bool configured = false;
   static int resident_per_sm = 0, sms = 0;
   if (!configured) {
@@ -491,7 +535,7 @@ static cudaError_t sweep_dispatch(int v, const DevParams &P, const FusedBuffers 
 template <int TX, int RS, int NH, int FORM, int NT, int MINB>
 static cudaError_t launch_sweep_batched_t(const BatchCase *cases, const WorkItem *work, int nwork, int parity,
                                           cudaStream_t st) {
-  const size_t smem = sizeof(PipeSmem<TX, RS, NH>);
+  const size_t smem = sizeof(PipeSmem<TX, RS, NH, FORM != 0>);
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_sweep_batched<TX, RS, NH, FORM, NT, MINB>,
