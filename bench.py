@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--batch-cases", type=int, default=128)
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the collapsed and FP16 state-form lines")
+    ap.add_argument("--no-three", action="store_true", help="skip the three-component line")
     ap.add_argument("--kernel-config", type=int, default=-1,
                     help="launch configuration of the step kernel (default: autotuned)")
     ap.add_argument("--stability", action="store_true",
@@ -293,6 +294,8 @@ def run_ours(args):
     if not args.no_forms:
         line["collapsed"] = run_state_form(args, torch, dev, stream, C, hbm, storage=0)
         line["fp16_storage"] = run_state_form(args, torch, dev, stream, C, hbm, storage=1)
+    if not args.no_three:
+        line["three_comp"] = run_three_comp(args, torch, dev, stream, hbm)
     if not args.no_batched:
         line["batched"] = run_batched(args, torch, dev, stream, rank, world, dist if world > 1 else None)
     if not args.no_surrogate and rank == 0:
@@ -347,6 +350,39 @@ def run_state_form(args, torch, dev, stream, C, hbm, storage):
     state = "FP16 g deviations + FP32 reference, C, tau" if storage else "g, C, tau (collapse_h = 1)"
     return {"state": state, "mlups": round(nodes / (ms * 1e3), 1), "ms_per_step": round(ms, 4),
             "bytes_per_node": bpn, "achieved_gbs": round(gbs, 1), "frac": round(gbs / hbm, 4), "kernel": name}
+
+
+def run_three_comp(args, torch, dev, stream, hbm):
+    """Three components (the set-up of the three-component configuration:
+    power-law matrix, two droplets of component 2, a bubble of component 3,
+    fully periodic, no gravity) on an nx x nx lattice, population and collapsed
+    state forms, each autotuned and timed with CUDA events like the main line."""
+    from paper_2207_09431_gb300 import lbm
+
+    nx = args.nx
+    p, discs = inputs.three_comp_case(nx)
+    C = inputs.bubble_fields(nx, nx, 3, p["xi"], discs, seed=0, noise=1e-8, periodic_y=True)
+    out = {"workload": f"three components {nx}x{nx}, fully periodic, droplets R = {discs[0][2]:g}, "
+                       f"{discs[1][2]:g} and bubble R = {discs[2][2]:g}"}
+    for form, collapse in (("populations", 0), ("collapsed", 1)):
+        q = dict(p, collapse_h=collapse)
+        lat = lbm.Lattice(q, device=dev, stream=stream)
+        lat.set_fields(C)
+        name = lat.autotune(reps=5)
+        lat.step(max(3, args.warmup))
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        lat.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev0.elapsed_time(ev1) / args.steps
+        bpn = 4 * 2 * (9 + (2 if collapse else 18) + 1)
+        gbs = bpn * nx * nx / (ms * 1e-3) / 1e9
+        out[form] = {"mlups": round(nx * nx / (ms * 1e3), 1), "ms_per_step": round(ms, 4), "bytes_per_node": bpn,
+                     "achieved_gbs": round(gbs, 1), "frac": round(gbs / hbm, 4), "kernel": name}
+        del lat
+    return out
 
 
 STEPS_TO_TERMINAL = 50000  # time steps a rising-bubble case needs to reach its terminal velocity
