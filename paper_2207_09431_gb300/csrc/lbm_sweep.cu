@@ -20,10 +20,12 @@
 // side) and at segment ends (3, 2, 1 rows per end).
 //
 // Each thread owns one item of every stage (NT >= RS (TX + 6)), with its
-// column fixed for the whole sweep.  The global loads of a step (state of
-// stage 0, g of stage 1, previous tau of stage 2) are issued first and used
-// last, after stage 3 and the collision, so their latency overlaps the
-// step's shared-memory work.
+// column fixed for the whole sweep and the ring slots of its rows kept in
+// registers.  The global loads of the next step (state of stage 0, g of stage
+// 1, previous tau of stage 2) are issued in the middle of a step, after stage
+// 1, and consumed in the next one, so their latency overlaps a whole step of
+// shared-memory work; a node's population directions lie at constant offsets
+// of one address (the interleaved layout of pop_index).
 //
 // Ghost rows beyond a wall (reading R10): stage 0 loads mirrored rows;
 // stencils of mu and p in stage 2 read the mirror row, which is the centre
