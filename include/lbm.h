@@ -299,7 +299,8 @@ lbm_status surr_predict(surr_net *n, const double *X, int rows, double *y_mean, 
  * hc: device pointer to the (ncomp - 1) x 9 planes of h (collapse_h == 0) or
  *     the (ncomp - 1) planes of C (collapse_h == 1).
  * pitch: floats per row (>= nx); plane_stride: floats per plane (>= pitch * ny);
- *     node (x, y) of plane q is at q * plane_stride + y * pitch + x.
+ *     node (x, y) of plane q is at q * plane_stride + y * pitch + x (planar,
+ *     not the interleaved layout a handle keeps its own populations in).
  * raw_out: host array of 15 doubles, the layout of lbm_postprocess.
  * cuda_stream: stream the two kernels run on; the call waits for it.
  * The first call on a device looks up the device address of the scratch
