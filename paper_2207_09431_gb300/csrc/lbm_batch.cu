@@ -72,6 +72,7 @@ struct lbm_batch {
       for (int y0 = 0; y0 < ny; y0 += ty)
         for (int x0 = 0; x0 < h[i]->dp.nx; x0 += tx) w.push_back({i, x0, y0, y0 + ty < ny ? y0 + ty : ny});
     }
+    if (w.size() > work_cap) return cudaErrorInvalidValue;  // the arena's work list is sized for 32 x 8 items
     *count = (int)w.size();
     if (w.empty()) return cudaSuccess;
     cudaError_t e = cudaMemcpyAsync(d_work, w.data(), w.size() * sizeof(lbm::WorkItem), cudaMemcpyHostToDevice,
