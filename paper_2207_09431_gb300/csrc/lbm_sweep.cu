@@ -63,6 +63,37 @@ struct PairVec<2> {
 // ring.  Used by the C state forms; the population form reads them again from
 // the ring, because the larger record would push the shared memory of three
 // CTAs past the carveout that leaves its (larger) loads in flight enough L1.
+// Post-collision populations of the 1-ring, stage 2 -> stage 3: stage 3 reads
+// g*_b and h*_b of one source node and direction together, so with one
+// h set they are one float2 per direction and node.
+template <int NH, int DB, int W1>
+struct PostRing {
+  float gs[9][DB][W1];
+  float hs[NH][9][DB][W1];
+  __device__ __forceinline__ void put(int a, int r, int c, float g, const float (&h)[NH][9]) {
+    gs[a][r][c] = g;
+#pragma unroll
+    for (int q = 0; q < NH; ++q) hs[q][a][r][c] = h[q][a];
+  }
+  __device__ __forceinline__ void get(int b, int r, int c, int a, float (&g)[9], float (&h)[NH][9]) const {
+    g[a] = gs[b][r][c];
+#pragma unroll
+    for (int q = 0; q < NH; ++q) h[q][a] = hs[q][b][r][c];
+  }
+};
+template <int DB, int W1>
+struct PostRing<1, DB, W1> {
+  float2 gh[9][DB][W1];
+  __device__ __forceinline__ void put(int a, int r, int c, float g, const float (&h)[1][9]) {
+    gh[a][r][c] = make_float2(g, h[0][a]);
+  }
+  __device__ __forceinline__ void get(int b, int r, int c, int a, float (&g)[9], float (&h)[1][9]) const {
+    const float2 v = gh[b][r][c];
+    g[a] = v.x;
+    h[0][a] = v.y;
+  }
+};
+
 template <int TX, int RS, int NH, bool REC>
 struct PipeSmem {
   using PV = PairVec<NH>;
@@ -79,8 +110,7 @@ struct PipeSmem {
   V mp[D2][W2];  // (mu_i, p) of the 2-ring
   // stage 2 -> stage 3: velocity of the collision node, g*, h*, sources
   float2 uvb[DB][W1];
-  float gs[9][DB][W1];
-  float hs[NH][9][DB][W1];
+  PostRing<NH, DB, W1> post;
   float svb[NH][DB][W1];
 };
 
@@ -282,9 +312,7 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
           const int ss = row_slot(-ey(a), sdn, s3, sup), cs = c3 + 1 - ex(a);  // source row r3 - e_a
-          gy[a] = s.gs[a][ss][cs];
-#pragma unroll
-          for (int q = 0; q < NH; ++q) hy[q][a] = s.hs[q][a][ss][cs];
+          s.post.get(a, ss, cs, a, gy, hy);
         }
       } else {
         const bool lo = r3 == 0, hi = r3 == ny - 1;
@@ -296,9 +324,7 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
           const int ss = bb ? s3 : row_slot(-ey(a), sdn, s3, sup);
           const int cs = bb ? c3 + 1 : c3 + 1 - ex(a);
           const int b = bb ? opp(a) : a;
-          gy[a] = s.gs[b][ss][cs];
-#pragma unroll
-          for (int q = 0; q < NH; ++q) hy[q][a] = s.hs[q][b][ss][cs];
+          s.post.get(b, ss, cs, a, gy, hy);
         }
       }
       store_node<NH, FORM>(P, B, plane, (long long)r3 * pitch + x3, gy, hy, svy, uv.x, uv.y);
@@ -378,9 +404,7 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
       node_collide<NH>(P, nc, pn, mun, g2, tprev, hs, sv, tn, gd2);
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
-        s.gs[a][s2b][c2] = g2[a];
-#pragma unroll
-        for (int q = 0; q < NH; ++q) s.hs[q][a][s2b][c2] = hs[q][a];
+        s.post.put(a, s2b, c2, g2[a], hs);
       }
 #pragma unroll
       for (int q = 0; q < NH; ++q) s.svb[q][s2b][c2] = sv[q];
