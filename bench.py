@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the collapsed and FP16 state-form lines")
     ap.add_argument("--no-three", action="store_true", help="skip the three-component line")
+    ap.add_argument("--state-form", default="populations", choices=["populations", "collapsed", "fp16"],
+                    help="state form of the main line (for profiling the other forms; the headline is the "
+                         "population form)")
     ap.add_argument("--kernel-config", type=int, default=-1,
                     help="launch configuration of the step kernel (default: autotuned)")
     ap.add_argument("--stability", action="store_true",
@@ -197,9 +200,14 @@ def kernel_bytes_per_node(nh: int) -> dict:
     }
 
 
-def step_bytes_per_node(nh: int) -> int:
-    """Algorithmic bytes of one time step: populations g (9), h (9 nh) and tau
-    read and written once."""
+def step_bytes_per_node(nh: int, form: str = "populations") -> int:
+    """Algorithmic bytes of one time step, every state array read and written
+    once: populations g (9), h (9 nh) and tau; or g, C (nh) and tau; or FP16 g
+    deviations (9 halves) with their FP32 reference, C and tau."""
+    if form == "collapsed":
+        return 4 * 2 * (9 + nh + 1)
+    if form == "fp16":
+        return 2 * (9 * 2 + 4 + 4 * nh + 4)
     return 4 * 2 * (9 + 9 * nh + 1)
 
 
@@ -215,9 +223,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     p, bubbles = inputs.sweep_case(args.nx)
+    form = args.state_form
+    if form != "populations":
+        p = dict(p, collapse_h=1, storage=1 if form == "fp16" else 0)
     nx, ny = p["nx"], p["ny"]
     nodes = nx * ny
     nh = p["ncomp"] - 1
+    sbpn = step_bytes_per_node(nh, form)
     C = inputs.bubble_fields(nx, ny, 2, p["xi"], bubbles, seed=rank, noise=1e-8)
     stream = torch.cuda.Stream(device=dev)
     lat = lbm.Lattice(p, device=dev, stream=stream)
@@ -255,15 +267,15 @@ def run_ours(args):
     bpn = kernel_bytes_per_node(nh)
     if kt:
         dom = max(kt, key=kt.get)
-        achieved = bpn.get(dom, step_bytes_per_node(nh)) * nodes / (kt[dom] * 1e-3) / 1e9
+        achieved = bpn.get(dom, sbpn) * nodes / (kt[dom] * 1e-3) / 1e9
     else:
         dom = "step"
-        achieved = step_bytes_per_node(nh) * nodes / (ms_max / args.steps * 1e-3) / 1e9
+        achieved = sbpn * nodes / (ms_max / args.steps * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": profiled_traffic(dom, nodes), "traffic_unit": "bytes per launch",
-                "step_bytes_per_node": step_bytes_per_node(nh),
-                "step_frac": round(step_bytes_per_node(nh) * nodes / (ms_max / args.steps * 1e-3) / 1e9 / hbm, 4)}
+                "traffic": profiled_traffic(dom if form == "populations" else f"{form}:{dom}", nodes),
+                "traffic_unit": "bytes per launch", "step_bytes_per_node": sbpn,
+                "step_frac": round(sbpn * nodes / (ms_max / args.steps * 1e-3) / 1e9 / hbm, 4)}
 
     # end to end through the C ABI with host buffers: upload the initial fields,
     # advance K steps, read back the observables
@@ -284,7 +296,7 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded rising bubble)",
-        "config": workload_config(nx, world),
+        "config": dict(workload_config(nx, world), **({} if form == "populations" else {"state_form": form})),
         "roofline": roofline, "e2e": e2e, "clocks": clk,
         "gpu_launches": lat.launches_per_step() * args.steps,
         "kernel_ms": {k: round(v, 5) for k, v in kt.items()},
