@@ -178,6 +178,31 @@ def profiled_traffic(kernel: str, nodes: int):
     return None if per_node is None else round(per_node * nodes)
 
 
+def profiled_inst_per_node(kernel: str):
+    """Thread instructions per node of `kernel` from the committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get("inst_per_node", {}).get(kernel)
+
+
+def issue_roofline(inst_per_node, mlups, sm_mhz):
+    """The step kernel's instruction issue against the issue peak of the GPU:
+    one warp instruction per cycle per scheduler, 4 schedulers per SM,
+    152 SMs, 32 lanes, at the SM clock sampled during the timed region."""
+    if inst_per_node is None or not sm_mhz:
+        return None
+    peak = 152 * 4 * 32 * sm_mhz * 1e6
+    achieved = inst_per_node * mlups * 1e6
+    return {"bound": "issue", "inst_per_node": inst_per_node, "achieved": round(achieved / 1e12, 2),
+            "peak": round(peak / 1e12, 2), "unit": "T thread instructions/s", "frac": round(achieved / peak, 4)}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -297,6 +322,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded rising bubble)",
         "config": dict(workload_config(nx, world), **({} if form == "populations" else {"state_form": form})),
+        "issue": issue_roofline(profiled_inst_per_node(dom if form == "populations" else f"{form}:{dom}"),
+                                value / world, clk.get("sm_max_mhz")),
         "roofline": roofline, "e2e": e2e, "clocks": clk,
         "gpu_launches": lat.launches_per_step() * args.steps,
         "kernel_ms": {k: round(v, 5) for k, v in kt.items()},
