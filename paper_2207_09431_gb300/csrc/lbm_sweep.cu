@@ -178,20 +178,34 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
   float ng[9];              // g of the next stage-1 item (FP32 forms)
   __half ngh[9];            // ... (FP16 form: deviations and reference)
   float nP = 0.f, nt = 0.f; // previous tau of the next stage-2 item
+  // A step is interior when the rows of its stage 0-2 items all lie inside
+  // the segment's halo and inside the lattice (the same for every thread):
+  // then every item is active, no row is mirrored and none wraps.  Used by the
+  // population form; the C forms ran slower with it (measured) and keep the
+  // general tests.
+  const int lo_row = max(ys - 1, 0), hi_row = min(ye + 3, ny);
+  auto interior = [&](int j) { return FORM == 0 && j + RS + 1 >= lo_row && j + 4 * RS + 3 <= hi_row; };
   auto item_rows = [&](int j, int &r0, int &r1, int &r2, bool &a0, bool &a1, bool &a2) {
     r0 = j + 3 * RS + 3 + d0;
     r1 = j + 2 * RS + 2 + d1;
     r2 = j + RS + 1 + d2;
-    a0 = v0 && r0 >= ys - 3 && r0 < ye + 3;
-    a1 = v1 && r1 >= ys - 2 && r1 < ye + 2 && (per || (r1 >= 0 && r1 < ny));
-    a2 = v2 && r2 >= ys - 1 && r2 < ye + 1 && (per || (r2 >= 0 && r2 < ny));
+    if (interior(j)) {
+      a0 = v0;
+      a1 = v1;
+      a2 = v2;
+    } else {
+      a0 = v0 && r0 >= ys - 3 && r0 < ye + 3;
+      a1 = v1 && r1 >= ys - 2 && r1 < ye + 2 && (per || (r1 >= 0 && r1 < ny));
+      a2 = v2 && r2 >= ys - 1 && r2 < ye + 1 && (per || (r2 >= 0 && r2 < ny));
+    }
   };
   auto issue = [&](int j) {
     int r0, r1, r2;
     bool a0, a1, a2;
     item_rows(j, r0, r1, r2, a0, a1, a2);
+    const bool in = interior(j);
     if (a0) {
-      const long long k0 = (long long)row_read(r0, ny, per) * pitch + x0c;
+      const long long k0 = (long long)(in ? r0 : row_read(r0, ny, per)) * pitch + x0c;
       if constexpr (FORM == 0) {
         const float *hp = B.h_in + pop_index(k0, 0, NS0);
 #pragma unroll
@@ -202,7 +216,7 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
       }
     }
     if (a1) {
-      const long long k1 = (long long)(per ? wrap_periodic(r1, ny) : r1) * pitch + x1c;
+      const long long k1 = (long long)(per && !in ? wrap_periodic(r1, ny) : r1) * pitch + x1c;
       if constexpr (FORM == 2) {
         const __half *gh = reinterpret_cast<const __half *>(B.g_in) + pop_index(k1, 0, 9);
         nP = B.g_in[(9 * plane) / 2 + k1];
@@ -214,7 +228,7 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
         for (int a = 0; a < 9; ++a) ng[a] = gp[a * 32];
       }
     }
-    if (a2) nt = B.tau_in[(long long)(per ? wrap_periodic(r2, ny) : r2) * pitch + x2c];
+    if (a2) nt = B.tau_in[(long long)(per && !in ? wrap_periodic(r2, ny) : r2) * pitch + x2c];
   };
   issue(j0);
 
@@ -224,7 +238,7 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
     item_rows(j, r0, r1, r2, a0, a1, a2);
     const int r3 = j + d3;
     const bool a3 = out3 && r3 >= ys && r3 < ye;
-    const long long k2 = (long long)(per ? wrap_periodic(r2, ny) : r2) * pitch + x2c;
+    const long long k2 = (long long)(per && !interior(j) ? wrap_periodic(r2, ny) : r2) * pitch + x2c;
 
     // ---- stage 0: C and rho of row r0 (3-ring column c0), from the loads of
     // the previous step
