@@ -48,6 +48,11 @@ def test_required_bytes_and_validation():
     assert nb >= (18 + 18 + 2 + 1 + 3 + 4 + 1) * plane
     bad = dict(p, ncomp=4)
     assert lbm.lbm_required_bytes(bad) == 0
+    # degenerate and oversized lattices
+    assert lbm.lbm_required_bytes(dict(p, nx=0)) == 0
+    assert lbm.lbm_required_bytes(dict(p, ny=2)) == 0
+    assert lbm.lbm_required_bytes(dict(p, nx=1, ny=3)) > 0
+    assert lbm.lbm_required_bytes(dict(p, nx=65536, ny=65536)) == 0
     assert lbm.lbm_required_bytes(dict(p, sigma12=1e-3, sigma13=1e-3, sigma23=3e-3)) == 0
     assert lbm.lbm_required_bytes(dict(p, tau_min=2.0, tau_max=1.0)) == 0
     assert lbm.lbm_required_bytes(dict(p, storage=7)) == 0

@@ -110,6 +110,20 @@ def test_variants_100_steps(lbm, mobility, fd_scheme):
     assert relerr(sv, ref) <= max(TOL, FLOOR_FACTOR * floor)
 
 
+@pytest.mark.parametrize("nx,ny,per", [(1, 3, 0), (3, 5, 0), (1, 4, 1), (2, 3, 1)])
+def test_degenerate_lattices(lbm, nx, ny, per):
+    """Lattices smaller than the stencils: one column (every x-neighbour is the
+    node itself), three rows between walls (every row next to a wall, the
+    ghost rows mirror the fluid ones), periodic lattices lower than the
+    five-row reach of a step; a smooth order-parameter pattern, 10 steps."""
+    p, _ = inputs.small_case()
+    p = dict(p, nx=nx, ny=ny, periodic_y=per)
+    C = inputs.round_to_fp32(0.5 + 0.3 * np.sin(np.arange(nx * ny, dtype=np.float64)).reshape(1, ny, nx))
+    c = Case(lbm, p, C)
+    c.step(10)
+    c.check()
+
+
 def test_small_rising_bubble_1000_steps(lbm):
     """64 x 128 rising bubble (R = 10, Eo = 10, n = 0.7, power law): fields and
     populations after 1000 steps; rise velocity within 0.5 %."""
