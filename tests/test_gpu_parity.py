@@ -121,7 +121,15 @@ def test_degenerate_lattices(lbm, nx, ny, per):
     C = inputs.round_to_fp32(0.5 + 0.3 * np.sin(np.arange(nx * ny, dtype=np.float64)).reshape(1, ny, nx))
     c = Case(lbm, p, C)
     c.step(10)
-    c.check()
+    if nx > 2:
+        c.check()
+        return
+    # one or two columns: the lattice is its own mirror image in x, so u_x is
+    # zero (exactly so in both oracle builds) and has no relative error to
+    # compare; it is bounded against u_y instead
+    c.check(names=("C1", "p", "uy", "tau", "g", "h"))
+    ux, uy = c.lat.field("ux"), c.lat.field("uy")
+    assert np.max(np.abs(ux)) <= 1e-6 * np.max(np.abs(uy))
 
 
 def test_small_rising_bubble_1000_steps(lbm):
