@@ -331,8 +331,11 @@ def run_ours(args):
         "observables_after": {"rise_velocity": obs["rise_velocity"], "mass1": obs["mass"][0]},
     }
     if not args.no_forms:
-        line["collapsed"] = run_state_form(args, torch, dev, stream, C, hbm, storage=0)
-        line["fp16_storage"] = run_state_form(args, torch, dev, stream, C, hbm, storage=1)
+        for key, storage, form in (("collapsed", 0, "collapsed"), ("fp16_storage", 1, "fp16")):
+            leg = run_state_form(args, torch, dev, stream, C, hbm, storage=storage)
+            leg["issue"] = issue_roofline(profiled_inst_per_node(f"{form}:{leg['kernel']}"), leg["mlups"],
+                                          clk.get("sm_max_mhz"))
+            line[key] = leg
     if not args.no_three:
         line["three_comp"] = run_three_comp(args, torch, dev, stream, hbm)
     if not args.no_batched:
