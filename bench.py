@@ -473,6 +473,8 @@ def run_batched(args, torch, dev, stream, rank=0, world=1, dist=None):
     return {"cases": len(all_cases), "nodes": nodes, "ranks": world,
             "density_ratio": all_cases[0][0]["rho"][0] / all_cases[0][0]["rho"][2],
             "ms_per_step": round(ms_batch, 4), "mlups": round(nodes / (ms_batch * 1e3), 1),
+            "achieved_gbs": round(step_bytes_per_node(1) * nodes / (ms_batch * 1e-3) / 1e9, 1),
+            "frac": round(step_bytes_per_node(1) * nodes / (ms_batch * 1e-3) / 1e9 / measured_peaks()[0], 4),
             "per_case_ms_per_step": round(ms_single, 4), "per_case_mlups": round(nodes / (ms_single * 1e3), 1),
             "speedup": round(ms_single / ms_batch, 3), "steps_to_terminal_assumed": STEPS_TO_TERMINAL,
             "cases_per_hour": round(len(all_cases) / hours_batch, 1),
