@@ -58,11 +58,6 @@ struct PairVec<2> {
   static __device__ __forceinline__ float last(const T &v) { return v.z; }
 };
 
-// REC: the collision's own C_i, rho, 1 / rho and the pair differences of rho
-// and C_i travel from stage 1 in the record, and stage 2 reads no (C, rho)
-// ring.  Used by the C state forms; the population form reads them again from
-// the ring, because the larger record would push the shared memory of three
-// CTAs past the carveout that leaves its (larger) loads in flight enough L1.
 // Post-collision populations of the 1-ring, stage 2 -> stage 3: stage 3 reads
 // g*_b and h*_b of one source node and direction together, so with one
 // h set they are one float2 per direction and node.
@@ -94,6 +89,11 @@ struct PostRing<1, DB, W1> {
   }
 };
 
+// REC: the collision's own C_i, rho, 1 / rho and the pair differences of rho
+// and C_i travel from stage 1 in the record, and stage 2 reads no (C, rho)
+// ring.  Used by the C state forms; the population form reads them again from
+// the ring, because the larger record would push the shared memory of three
+// CTAs past the carveout that leaves its (larger) loads in flight enough L1.
 template <int TX, int RS, int NH, bool REC>
 struct PipeSmem {
   using PV = PairVec<NH>;
