@@ -176,8 +176,9 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
   constexpr int NS0 = FORM == 0 ? 9 * NH : NH;
   float nh[NS0];            // state values of the next stage-0 item
   float ng[9];              // g of the next stage-1 item (FP32 forms)
-  __half ngh[9];            // ... (FP16 form: deviations and reference)
-  float nP = 0.f, nt = 0.f; // previous tau of the next stage-2 item
+  __half ngh[9];            // ... (FP16 form: the nine deviations
+  float nP = 0.f;           //      and their FP32 reference)
+  float nt = 0.f;           // previous tau of the next stage-2 item
   // A step is interior when the rows of its stage 0-2 items all lie inside
   // the segment's halo and inside the lattice (the same for every thread):
   // then every item is active, no row is mirrored and none wraps.  Used by the
