@@ -292,22 +292,26 @@ lbm_status surr_predict(surr_net *n, const double *X, int rows, double *y_mean, 
  * it already holds.  This call allocates nothing (no cudaMalloc, cudaFree or
  * allocating library routine): its reduction scratch is a fixed array of about
  * 416 KiB that every GPU loading the library keeps until the process exits.
- * The paper has no counterpart; the sums are those of lbm_observables.
+ * The paper has no counterpart; the sums are those of lbm_observables, for
+ * every lattice form lbm_create accepts with FP32 populations (two or three
+ * components, walls or periodic y, periodic or open x).
  *
- * p: lattice parameters (nx * ny <= LBM_STATIC_MAX_NODES, else LBM_E_RANGE).
- * g: device pointer to the 9 planes of the populations g (Eq. 14-16).
+ * p: lattice parameters, checked as lbm_create checks them (LBM_E_INVAL), with
+ *     storage == 0; nx * ny <= LBM_STATIC_MAX_NODES, else LBM_E_RANGE.
+ * g: device pointer to the 9 planes of the populations g.
  * hc: device pointer to the (ncomp - 1) x 9 planes of h (collapse_h == 0) or
  *     the (ncomp - 1) planes of C (collapse_h == 1).
  * pitch: floats per row (>= nx); plane_stride: floats per plane (>= pitch * ny);
  *     node (x, y) of plane q is at q * plane_stride + y * pitch + x (planar,
  *     not the interleaved layout a handle keeps its own populations in).
  * raw_out: host array of 15 doubles, the layout of lbm_postprocess.
- * cuda_stream: stream the two kernels run on; the call waits for it.
+ * cuda_stream: stream the two kernels run on; the call copies the sums to
+ *     the host and waits for the stream, so it cannot be issued while that
+ *     stream is being captured into a CUDA graph (LBM_E_INVAL).
  * The first call on a device looks up the device address of the scratch
- * array; make it before any stream capture on that device.  Calls that
- * overlap on the GPU (other streams, other host threads) race on the shared
- * scratch array.  Returns LBM_E_INVAL for bad arguments, LBM_E_CUDA if a CUDA
- * call fails. */
+ * array.  Every call shares that array: calls that overlap on the GPU (other
+ * streams, other host threads) race on it.  Returns LBM_E_INVAL for bad
+ * arguments, LBM_E_CUDA if a CUDA call fails. */
 lbm_status lbm_observables_static(const lbm_params *p, const float *g, const float *hc, int pitch,
                                   long long plane_stride, double raw_out[15], void *cuda_stream);
 

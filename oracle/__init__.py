@@ -11,6 +11,8 @@ and wraps it with ctypes.
 
 Parity status per function (what pins it lives in ``tests/test_oracle_pins.py``):
   step / set_fields / init_bubbles   pinned (closed forms, invariants, hand step)
+  raw observable sums                pinned (prescribed symmetric disc: centroid,
+                                     mean velocity, masses, brute-force extents)
   observables post-processing        pinned (Tables 5-7 of the paper)
 """
 from __future__ import annotations

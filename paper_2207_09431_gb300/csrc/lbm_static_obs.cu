@@ -23,11 +23,12 @@
 
 #include "lbm.h"
 #include "lbm_device.cuh"
+#include "lbm_internal.h"
 
 namespace lbm {
 namespace {
 
-constexpr int kBlockNodes = 256;  // 32 x 8 nodes per block
+constexpr int kBlockNodes = 256;  // 256 consecutive nodes (row-major, x fastest) per block
 constexpr int kMaxBlocks = LBM_STATIC_MAX_NODES / kBlockNodes;
 constexpr int kSums = 11;          // M1..3, M1..3 above 0.5, A, sum Cx, sum Cy, sum C ux, sum C uy
 constexpr int kExt = 4;            // xmin, -xmax, ymin, -ymax
@@ -45,6 +46,13 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 StaticScratch *g_scratch_ptr[kMaxDevices] = {};
 
+// Column seen at x for offsets of one column: periodic, or (open x) the
+// mirror ghost columns beyond the inlet and outlet, as the step kernels see it.
+__device__ __forceinline__ int column_at(const DevParams &P, int x) {
+  if (!P.open_x) return wrap_x(x, P.nx);
+  return x < 0 ? -1 - x : (x >= P.nx ? 2 * P.nx - 1 - x : x);
+}
+
 // C_1..C_3 at node k from the populations (Eq. 22) or from the stored C.
 __device__ __forceinline__ void order_params(const DevParams &P, const float *hc, int collapse, long long k,
                                              float C[3]) {
@@ -61,20 +69,23 @@ __device__ __forceinline__ void order_params(const DevParams &P, const float *hc
   C[2] = 1.0f - C[0] - C[1];
 }
 
-// One block per 32 x 8 nodes: C, u (Eq. 23, with mu from Eq. 5) and the
-// block's partial sums, written to its own row of the scratch array.
+// One block per 256 consecutive nodes of the row-major order (so that
+// ceil(nx ny / 256) rows of the scratch array suffice for any shape): C, u
+// (Eq. 23, with mu from Eq. 5) and the block's partial sums, written to its
+// own row of the scratch array.
 __global__ void k_obs_partial(DevParams P, const float *__restrict__ g, const float *__restrict__ hc, int collapse,
                               int gas_comp, StaticScratch *scr) {
-  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
-  const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+  const long long node = (long long)blockIdx.x * kBlockNodes + threadIdx.x;
+  const int blk = blockIdx.x;
   double v[kSums];
   for (int q = 0; q < kSums; ++q) v[q] = 0.0;
   int e[kExt] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
-  if (x < P.nx && y < P.ny) {
+  if (node < (long long)P.nx * P.ny) {
+    const int x = (int)(node % P.nx), y = (int)(node / P.nx);
     const long long k = (long long)y * P.pitch + x;
     float Cn[9][3], rn[9];
     for (int a = 0; a < 9; ++a) {
-      const int xs = wrap_x(x + ex(a), P.nx), ys = wrap_y(y + ey(a), P.ny, P.periodic_y);
+      const int xs = column_at(P, x + ex(a)), ys = wrap_y(y + ey(a), P.ny, P.periodic_y);
       order_params(P, hc, collapse, (long long)ys * P.pitch + xs, Cn[a]);
       rn[a] = rho_of(P, Cn[a][0], Cn[a][1], Cn[a][2]);
     }
@@ -126,24 +137,25 @@ __global__ void k_obs_partial(DevParams P, const float *__restrict__ g, const fl
   // fixed-order reduction: warp shuffles, then the 8 warp results in order
   __shared__ double ws[8][kSums];
   __shared__ int we[8][kExt];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int off = 16; off > 0; off >>= 1) {
     for (int q = 0; q < kSums; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
     for (int q = 0; q < kExt; ++q) e[q] = min(e[q], __shfl_down_sync(0xffffffffu, e[q], off));
   }
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < kSums; ++q) ws[threadIdx.y][q] = v[q];
-    for (int q = 0; q < kExt; ++q) we[threadIdx.y][q] = e[q];
+  if (lane == 0) {
+    for (int q = 0; q < kSums; ++q) ws[warp][q] = v[q];
+    for (int q = 0; q < kExt; ++q) we[warp][q] = e[q];
   }
   __syncthreads();
-  if (threadIdx.y == 0 && threadIdx.x < kSums) {
+  if (warp == 0 && lane < kSums) {
     double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += ws[w][threadIdx.x];
-    scr->partial[blk][threadIdx.x] = s;
+    for (int w = 0; w < 8; ++w) s += ws[w][lane];
+    scr->partial[blk][lane] = s;
   }
-  if (threadIdx.y == 1 && threadIdx.x < kExt) {
+  if (warp == 1 && lane < kExt) {
     int m = 0x7fffffff;
-    for (int w = 0; w < 8; ++w) m = min(m, we[w][threadIdx.x]);
-    scr->ext[blk][threadIdx.x] = m;
+    for (int w = 0; w < 8; ++w) m = min(m, we[w][lane]);
+    scr->ext[blk][lane] = m;
   }
 }
 
@@ -177,8 +189,7 @@ __global__ void k_obs_total(int nblocks, StaticScratch *scr) {
 }
 
 // Device address of the scratch array on the current device, looked up once
-// per device (the first call on a device does it; make that first call before
-// any stream capture on the device).
+// per device by the first call made on it.
 cudaError_t scratch_on_current_device(StaticScratch **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -201,47 +212,26 @@ cudaError_t scratch_on_current_device(StaticScratch **out) {
 extern "C" lbm_status lbm_observables_static(const lbm_params *p, const float *g, const float *hc, int pitch,
                                              long long plane_stride, double raw_out[15], void *cuda_stream) {
   if (!p || !g || !hc || !raw_out) return LBM_E_INVAL;
-  if (p->nx < 1 || p->ny < 3 || (p->ncomp != 2 && p->ncomp != 3) || (p->gas_comp != 2 && p->gas_comp != 3))
-    return LBM_E_INVAL;
+  if (validate(p)) return LBM_E_INVAL;
+  if (p->storage != 0) return LBM_E_INVAL;  // g is read as FP32 planes
   if (pitch < p->nx || plane_stride < (long long)pitch * p->ny) return LBM_E_INVAL;
   if ((long long)p->nx * p->ny > LBM_STATIC_MAX_NODES) return LBM_E_RANGE;
-  const int bx = (p->nx + 31) / 32, by = (p->ny + 7) / 8;
-  if (bx * by > lbm::kMaxBlocks) return LBM_E_RANGE;
-  lbm::DevParams d{};
-  d.nx = p->nx;
-  d.ny = p->ny;
-  d.pitch = pitch;
-  d.ncomp = p->ncomp;
-  d.nh = p->ncomp - 1;
-  d.periodic_y = p->periodic_y ? 1 : 0;
-  for (int i = 0; i < 3; ++i) d.rho[i] = (float)p->rho[i];
-  d.sig12 = (float)p->sigma12;
-  d.sig13 = (float)p->sigma13;
-  d.sig23 = (float)p->sigma23;
-  d.Lambda = (float)p->Lambda;
-  const double S1 = p->sigma12 + p->sigma13 - p->sigma23;
-  const double S2 = p->sigma12 + p->sigma23 - p->sigma13;
-  const double S3 = p->sigma13 + p->sigma23 - p->sigma12;
-  if (!(S1 > 0 && S2 > 0 && S3 > 0) || !(p->xi > 0)) return LBM_E_INVAL;
-  d.Sig[0] = (float)S1;
-  d.Sig[1] = (float)S2;
-  d.Sig[2] = (float)S3;
-  d.SigT = (float)(3.0 / (1.0 / S1 + 1.0 / S2 + 1.0 / S3));
-  d.xi = (float)p->xi;
-  const double Sg[3] = {S1, S2, S3};
-  for (int i = 0; i < 3; ++i) {
-    d.inv_sig[i] = (float)(1.0 / Sg[i]);
-    d.grad_coef[i] = (float)(0.75 * p->xi * Sg[i]);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  {
+    // the call reads its results back and waits for the stream, which a
+    // capturing stream does not allow
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return LBM_E_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return LBM_E_INVAL;
   }
-  d.mu_pre = (float)(4.0 * (3.0 / (1.0 / S1 + 1.0 / S2 + 1.0 / S3)) / p->xi);
-  d.gravity = (float)p->gravity;
-  d.force_x = (float)p->force_x;
+  const int nblocks = (int)(((long long)p->nx * p->ny + lbm::kBlockNodes - 1) / lbm::kBlockNodes);
+  lbm::DevParams d = dev_params(*p);
+  d.pitch = pitch;
   d.plane = plane_stride;
   lbm::StaticScratch *scr = nullptr;
   if (lbm::scratch_on_current_device(&scr) != cudaSuccess) return LBM_E_CUDA;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  lbm::k_obs_partial<<<dim3(bx, by), dim3(32, 8), 0, s>>>(d, g, hc, p->collapse_h ? 1 : 0, p->gas_comp, scr);
-  lbm::k_obs_total<<<1, 256, 0, s>>>(bx * by, scr);
+  lbm::k_obs_partial<<<nblocks, lbm::kBlockNodes, 0, s>>>(d, g, hc, p->collapse_h ? 1 : 0, p->gas_comp, scr);
+  lbm::k_obs_total<<<1, 256, 0, s>>>(nblocks, scr);
   double total[lbm::kSums];
   int ext[lbm::kExt];
   cudaError_t e = cudaGetLastError();

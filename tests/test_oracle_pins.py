@@ -373,6 +373,59 @@ def test_observable_formulas_against_tables_5_to_7():
 
 
 # ------------------------------------------------------------------ inputs
+# ------------------------------------------------------------------ P9b
+@pytest.mark.parametrize("ncomp", [2, 3])
+def test_observable_sums_of_prescribed_disc(ncomp):
+    """Raw observable sums (Sec. 3.1 masses, Eq. 43-44 centroid and mean
+    velocity, the C_g > 0.5 extents behind the aspect ratio of Eq. 41) of a
+    state whose answers are fixed without the oracle.
+
+    A gas disc centred between nodes, (31.5, 47.5), on a 64 x 96 lattice is
+    mirror-symmetric about both centre lines, so its C_g-weighted centroid is
+    the centre.  The state is set with a uniform velocity (u_x, u_y) =
+    (0.011, -0.0037) and no step is taken: the equilibria of Eq. 16 return
+    that velocity through Eq. 23 (their first moment is rho u minus half the
+    force), so sum C_g u / sum C_g is the prescribed velocity.  C_g > 0.5
+    exactly where the tanh profile has r < R, so the extents are those of the
+    nodes inside the circle, counted here by brute force.  The masses are the
+    plain sums of the fields that were set.  Different x and y (centre,
+    velocity, lattice sides) catch a swap of the axes; the extents catch an
+    off-by-one."""
+    nx, ny, R, xi = 64, 96, 10.3, 4.0
+    cx, cy = 31.5, 47.5
+    ux0, uy0 = 0.011, -0.0037
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    r = np.hypot(x - cx, y - cy)
+    cg = 0.5 - 0.5 * np.tanh((r - R) / (0.5 * xi))
+    if ncomp == 2:
+        C = (1.0 - cg)[None]
+        comps = [1.0 - cg, np.zeros_like(cg), cg]
+    else:  # a droplet of component 2 in the lower half, the gas disc as above
+        c2 = 0.5 - 0.5 * np.tanh((np.hypot(x - 20.0, y - 15.0) - 6.2) / (0.5 * xi))
+        C = np.stack([1.0 - cg - c2, c2])
+        comps = [1.0 - cg - c2, c2, cg]
+    p = dict(nx=nx, ny=ny, ncomp=ncomp, rho=(1.0, 1.0, 0.05), tau=(0.8, 0.8, 0.5), gravity=1e-6,
+             sigma12=1e-3, sigma13=1e-3, sigma23=1e-3, xi=xi)
+    o = oracle.Oracle(p)
+    o.set_fields(C, ux=np.full((ny, nx), ux0), uy=np.full((ny, nx), uy0))
+    raw = o.raw_observables(gas_comp=3)
+    for i in range(3):
+        assert raw[i] == pytest.approx(comps[i].sum(), rel=1e-13, abs=1e-10)
+        assert raw[3 + i] == pytest.approx(comps[i][comps[i] > 0.5].sum(), rel=1e-13, abs=1e-10)
+    A = raw[6]
+    assert A == pytest.approx(cg.sum(), rel=1e-13)
+    assert raw[7] / A == pytest.approx(cx, abs=1e-9)
+    assert raw[8] / A == pytest.approx(cy, abs=1e-9)
+    assert raw[9] / A == pytest.approx(ux0, rel=1e-9)
+    assert raw[10] / A == pytest.approx(uy0, rel=1e-9)
+    inside = [(i, j) for j in range(ny) for i in range(nx) if (i - cx) ** 2 + (j - cy) ** 2 < R * R]
+    xs = [i for i, _ in inside]
+    ys = [j for _, j in inside]
+    assert list(raw[11:]) == [min(xs), max(xs), min(ys), max(ys)]
+    assert (max(xs) - min(xs), max(ys) - min(ys)) == (19, 19)   # |dx|, |dy| <= 9.5 inside R = 10.3
+
+
 def test_splitmix64_reference_vectors():
     t = _golden("splitmix64_vectors.json")
     for v in t["vectors"]:
