@@ -220,7 +220,8 @@ lbm_status lbm_postprocess(const lbm_params *p, const double raw[15], lbm_obs *o
  * one kernel launch per time step covers every tile of every active case
  * (a work list of (case, tile) items), and runs of 16 steps are replayed from a
  * captured CUDA graph (on a created stream; on the legacy or per-thread default
- * stream the steps are launched directly).  All cases share ncomp and collapse_h and use
+ * stream the steps are launched directly); or, in persistent mode
+ * (lbm_batch_set_persistent), one launch covers thousands of steps.  All cases share ncomp and collapse_h and use
  * fd_scheme 0 and storage 0.  Each case is an ordinary handle carved from the batch arena:
  * set its initial state, read its observables, fields and checkpoints with the
  * single-lattice calls on lbm_batch_case(b, i); lbm_step on a case advances that
@@ -240,8 +241,24 @@ lbm_status lbm_batch_set_active(lbm_batch *b, int i, int active);
  * case that produced a non-finite value is deactivated and the call returns
  * LBM_E_DIVERGED naming it in lbm_batch_last_error; the others advanced. */
 lbm_status lbm_batch_step(lbm_batch *b, long long nsteps);
-/* As lbm_autotune, over the whole work list; states are not advanced. */
+/* As lbm_autotune, over the whole work list; states are not advanced.  In
+ * persistent mode only the sweep configurations are candidates. */
 lbm_status lbm_batch_autotune(lbm_batch *b, int reps, int *chosen);
+/* Persistent mode (on = 1; 0 returns to one launch per step).  lbm_batch_step
+ * then advances the whole ensemble in persistent cooperative launches of up to
+ * 4096 steps each (whole launches replayed from a captured CUDA graph on a
+ * created stream): as many CTAs as fit on the device at once share the work
+ * items (case, strip, row segment) of a step and meet at a grid barrier before
+ * the next step.  The node values are those of the per-step launches, bit for
+ * bit (same per-node arithmetic, same items).  Every barrier wait polls at most
+ * spin_limit times (0: the default, about a second or more; a wait is expected
+ * to last microseconds) and then stops the launch without fault: lbm_batch_step
+ * returns LBM_E_TIMEOUT, and because the launch stopped part-way through a
+ * step, every active case is marked uninitialised and must be set again
+ * (lbm_set_fields, lbm_init_bubbles or lbm_load on lbm_batch_case) before it
+ * is stepped.  This mode extends the paper's method to ensembles (Sec. 4.3 runs
+ * its cases one by one). */
+lbm_status lbm_batch_set_persistent(lbm_batch *b, int on, long long spin_limit);
 void lbm_batch_destroy(lbm_batch *b);
 const char *lbm_batch_last_error(const lbm_batch *b);
 

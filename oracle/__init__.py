@@ -30,16 +30,22 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATHS = {"f64": os.path.join(_BUILD_DIR, "liblbm_oracle.so"),
-              "f32": os.path.join(_BUILD_DIR, "liblbm_oracle_f32.so")}
+              "f32": os.path.join(_BUILD_DIR, "liblbm_oracle_f32.so"),
+              "f64-omp": os.path.join(_BUILD_DIR, "liblbm_oracle_omp.so"),
+              "f32-omp": os.path.join(_BUILD_DIR, "liblbm_oracle_f32_omp.so")}
 _libs = {}
 
 
 def build(force: bool = False, precision: str = "f64") -> str:
-    """Compile the oracle into a shared library (gcc, no machine-specific flags).
+    """Compile the oracle into a shared library (gcc -O3, no machine-specific
+    flags, ISO C so that no multiply-add is contracted).
 
     precision "f64" is the oracle.  "f32" compiles the same source with FP32
     internals; the GPU parity tests use it only to measure the FP32 rounding
-    floor of the scheme on a case."""
+    floor of the scheme on a case.  "f64-omp" and "f32-omp" are those builds
+    with OpenMP, whose whole-field passes share their nodes among the host's
+    threads (the same results, bit for bit): the timed CPU baseline and the
+    tests on paper-size lattices use them."""
     os.makedirs(_BUILD_DIR, exist_ok=True)
     path = _LIB_PATHS[precision]
     if (not force and os.path.exists(path)
@@ -47,9 +53,11 @@ def build(force: bool = False, precision: str = "f64") -> str:
         return path
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_BUILD_DIR)
     os.close(fd)
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
-    if precision == "f32":
+    cmd = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    if precision.startswith("f32"):
         cmd.insert(1, "-DORACLE_REAL=float")
+    if precision.endswith("-omp"):
+        cmd.insert(1, "-fopenmp")
     subprocess.run(cmd, check=True)
     os.replace(tmp, path)
     return path

@@ -38,9 +38,15 @@
  *       previous step's node tau (Sec. 2.3, text after Eq. 32).
  *   R7  the sum inside Eq. 18 runs over a separate index j (same force for
  *       every i).
- *   R8  the variable-mobility term of Eq. 18 is the scalar
- *       (D0/Sigma_i)(1 - 2 C_i) grad C_i . grad mu_i; it is absent for the
- *       constant mobility.
+ *   R8  the variable mobility of Eq. 6 is (D0/Sigma_i) c_i (1 - c_i) with
+ *       c_i = clip(C_i, 0, 1): with C_i itself the mobility turns negative
+ *       (backward diffusion) wherever C_i leaves [0, 1], which the
+ *       Cahn-Hilliard bulk shift of a curved interface does inside every
+ *       bubble (C_i ~ -xi/(24 R)); every paper-size case then diverges within
+ *       1000 steps.  The variable-mobility term of Eq. 18 is the derivative
+ *       of that mobility: the scalar (D0/Sigma_i)(1 - 2 C_i) grad C_i .
+ *       grad mu_i where 0 <= C_i <= 1, else 0; it is absent for the constant
+ *       mobility.
  *   R9  the destination-side terms of Eq. 18 are added at the node where each
  *       population actually arrives, bounced ones included.
  *   R10 half-way walls at y = -1/2 and y = ny - 1/2; stencils read ghost rows
@@ -78,6 +84,12 @@
 #ifndef ORACLE_REAL
 #define ORACLE_REAL double
 #endif
+
+/* Whole-field passes treat every node independently (each node's own sums
+ * keep their order), so a build with -fopenmp may share a pass's nodes among
+ * threads without changing a single result; without -fopenmp the pragma is
+ * ignored.  Only the timed CPU baseline uses that build. */
+#define ORC_NODE_LOOP _Pragma("omp parallel for schedule(static)")
 typedef ORACLE_REAL real;
 
 typedef struct {
@@ -164,6 +176,7 @@ static real at(const orc_state *s, const real *f, size_t k, int a, int d) {
 
 /* Isotropic gradient (reading R2). */
 static void grad_iso(const orc_state *s, const real *f, real *gx, real *gy) {
+  ORC_NODE_LOOP
   for (size_t k = 0; k < s->n; ++k) {
     real sx = 0.0, sy = 0.0;
     for (int a = 0; a < 9; ++a) {
@@ -178,6 +191,7 @@ static void grad_iso(const orc_state *s, const real *f, real *gx, real *gy) {
 
 /* Isotropic Laplacian (reading R2). */
 static void lap_iso(const orc_state *s, const real *f, real *out) {
+  ORC_NODE_LOOP
   for (size_t k = 0; k < s->n; ++k) {
     real c = f[k], acc = 0.0;
     for (int a = 0; a < 9; ++a) acc += W[a] * (at(s, f, k, a, 1) - c);
@@ -258,6 +272,7 @@ static real tau_mixture(const orc_state *s, size_t k, real tau1) {
  * u (Eq. 23) and p (Eq. 24 with R3). */
 static void compute_macros(orc_state *s) {
   const size_t n = s->n;
+  ORC_NODE_LOOP
   for (size_t k = 0; k < n; ++k) {
     real c[2] = {0.0, 0.0};
     for (int i = 0; i < s->nh; ++i)
@@ -268,6 +283,7 @@ static void compute_macros(orc_state *s) {
     s->rho[k] = rho_mixture(s, s->C[0][k], s->C[1][k], s->C[2][k]);
   }
   for (int i = 0; i < 3; ++i) lap_iso(s, s->C[i], s->lapC[i]);
+  ORC_NODE_LOOP
   for (size_t k = 0; k < n; ++k) {
     real d[3];
     dE0(s, s->C[0][k], s->C[1][k], s->C[2][k], d);
@@ -280,6 +296,7 @@ static void compute_macros(orc_state *s) {
   }
   for (int i = 0; i < 3; ++i) grad_iso(s, s->C[i], s->gCx[i], s->gCy[i]);
   grad_iso(s, s->rho, s->grx, s->gry);
+  ORC_NODE_LOOP
   for (size_t k = 0; k < n; ++k) {
     real fx = 0.0, fy = 0.0;
     for (int j = 0; j < 3; ++j) {
@@ -334,6 +351,7 @@ static real forcing_h(const orc_state *s, int i, size_t k, int a) {
 static void directional_fields(orc_state *s) {
   const size_t n = s->n;
   for (int a = 0; a < 9; ++a)
+    ORC_NODE_LOOP
     for (size_t k = 0; k < n; ++k) {
       size_t ak = (size_t)a * n + k;
       s->drho[ak] = dir_deriv(s, s->rho, k, a);
@@ -348,6 +366,7 @@ static void directional_fields(orc_state *s) {
 static void forcing_and_equilibria(orc_state *s) {
   const size_t n = s->n;
   for (int a = 0; a < 9; ++a)
+    ORC_NODE_LOOP
     for (size_t k = 0; k < n; ++k) {
       size_t ak = (size_t)a * n + k;
       real G = Gamma(a, s->ux[k], s->uy[k]);
@@ -628,6 +647,7 @@ static void one_step(orc_state *s) {
    * reading R4).  f^neq follows Eq. 29; Eq. 25's denominator 2 (tau + 1/2)
    * rho cs^2 belongs to the barred populations, so with the un-barred f^neq of
    * Eq. 29 it is 2 tau rho cs^2 (the two forms give the same D). */
+  ORC_NODE_LOOP
   for (size_t k = 0; k < n; ++k) {
     real tp = s->tau[k];
     real Pxx = 0.0, Pyy = 0.0, Pxy = 0.0;
@@ -648,12 +668,17 @@ static void one_step(orc_state *s) {
   /* Diffusion sources of Eq. 18: S_i = D_i lap(mu_i) (Eq. 6) and, for the
    * variable mobility, V_i of Eq. 21 (reading R8). */
   for (int i = 0; i < s->nh; ++i)
+    ORC_NODE_LOOP
     for (size_t k = 0; k < n; ++k) {
       real Ci = s->C[i][k];
       real D = s->p.D0 / s->Sig[i];
-      if (s->p.mobility == 1) D *= Ci * (1.0 - Ci);
+      /* reading R8: the mobility of Eq. 6 with C_i clipped to [0, 1], and V_i
+       * the derivative of that mobility, zero where C_i lies outside */
+      real ci = Ci < 0.0 ? 0.0 : (Ci > 1.0 ? 1.0 : Ci);
+      int inside = Ci >= 0.0 && Ci <= 1.0;
+      if (s->p.mobility == 1) D *= ci * (1.0 - ci);
       s->S[i][k] = D * s->lapmu[i][k];
-      s->V[i][k] = (s->p.mobility == 1)
+      s->V[i][k] = (s->p.mobility == 1 && inside)
                        ? s->p.D0 / s->Sig[i] * (1.0 - 2.0 * Ci) *
                              (s->gCx[i][k] * s->gmux[i][k] + s->gCy[i][k] * s->gmuy[i][k])
                        : 0.0;
@@ -661,6 +686,7 @@ static void one_step(orc_state *s) {
   /* Collision (Eq. 14 and Eq. 18 with tau_h = 0.5, source-side terms). */
   const real tau_h = 0.5;
   for (int a = 0; a < 9; ++a)
+    ORC_NODE_LOOP
     for (size_t k = 0; k < n; ++k) {
       size_t ak = (size_t)a * n + k;
       real ga = s->g[ak];
@@ -684,6 +710,7 @@ static void one_step(orc_state *s) {
   /* Streaming: population a arriving at y left y - e_a; across a wall it is
    * the population leaving y in the opposite direction (half-way bounce-back),
    * then the destination-side terms of Eq. 18 at the arrival node (R9). */
+  ORC_NODE_LOOP
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       size_t k = idx(s, x, y);

@@ -1,7 +1,9 @@
 // Batched ensemble of lattices (many rising-bubble cases of different sizes
 // and parameters): every active case advances in one kernel launch per time
 // step over a work list of (case, tile) items, and runs of steps are replayed
-// from a captured CUDA graph.  Each case is an ordinary lbm_handle carved from
+// from a captured CUDA graph; or (persistent mode) in one cooperative launch
+// for thousands of steps, whose CTAs share each step's work items and meet at
+// a bounded grid barrier between steps, replayed from a captured graph too.  Each case is an ordinary lbm_handle carved from
 // the batch arena, so initial conditions, observables, fields and checkpoints
 // use the single-lattice calls on lbm_batch_case(b, i).
 #include <cuda_runtime.h>
@@ -16,9 +18,16 @@
 namespace {
 
 constexpr int kGraphSteps = 16;  // time steps per captured graph (even: parity returns)
+// time steps per persistent launch (even); about 2 s for 128 cases of up to
+// 300 x 600, so a launch stays short and a run of steps is a few graph replays
+constexpr int kPersistSteps = 4096;
+// polls of a grid-barrier wait before it gives up (each poll sleeps ~64 ns and
+// reads two words from L2: well over a second, against microseconds expected)
+constexpr long long kDefaultSpinLimit = 1LL << 22;
 
 size_t batch_table_bytes(int n) { return align_up((size_t)n * sizeof(lbm::BatchCase), kAlign); }
 size_t batch_err_bytes(int n) { return align_up((size_t)n * sizeof(unsigned), kAlign); }
+size_t batch_sync_bytes() { return align_up(sizeof(lbm::GridSync), kAlign); }
 
 // Upper bound of work items: tiles of the smallest tile shape.
 size_t max_work(const lbm_params *cases, int n) {
@@ -37,6 +46,12 @@ struct lbm_batch {
   lbm::BatchCase *d_cases = nullptr;
   lbm::WorkItem *d_work = nullptr;
   unsigned *d_err = nullptr;
+  lbm::GridSync *d_sync = nullptr;
+  bool persistent = false;
+  long long spin_limit = kDefaultSpinLimit;
+  cudaGraphExec_t pgraph = nullptr;  // one persistent launch of kPersistSteps steps
+  int pgraph_nwork = -1, pgraph_variant = -1;
+  long long pgraph_limit = -1;
   size_t work_cap = 0;
   int nwork = 0;
   int variant = 0;
@@ -57,6 +72,7 @@ struct lbm_batch {
   }
   ~lbm_batch() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (pgraph) cudaGraphExecDestroy(pgraph);
     for (auto *x : h) delete x;
   }
 
@@ -98,6 +114,92 @@ struct lbm_batch {
   }
 };
 
+// Persistent mode of lbm_batch_step: whole launches of kPersistSteps steps
+// replayed from a captured graph (barrier state reset, then the launch), the
+// remainder in one direct launch; then the error words and the barrier status.
+static lbm_status persistent_steps(lbm_batch *b, long long nsteps) {
+  if (!lbm::batched_variant_is_sweep(b->nh, b->variant))
+    return b->fail(LBM_E_STATE, "persistent mode runs sweep configurations (autotune in persistent mode)");
+  cudaError_t e = cudaSuccess;
+  int grid = 0;
+  auto one_launch = [&](int steps) {
+    cudaError_t r = cudaMemsetAsync(b->d_sync, 0, sizeof(lbm::GridSync), b->stream);
+    if (r == cudaSuccess)
+      r = lbm::launch_sweep_persistent(b->nh, b->collapse, b->d_cases, b->d_work, b->nwork, 0, steps, b->d_sync,
+                                       b->spin_limit, b->stream, b->variant, &grid);
+    return r;
+  };
+  const bool capturable = b->stream != nullptr && b->stream != cudaStreamLegacy && b->stream != cudaStreamPerThread;
+  const long long full = capturable ? nsteps / kPersistSteps : 0;
+  if (full > 0 && (!b->pgraph || b->pgraph_nwork != b->nwork || b->pgraph_variant != b->variant ||
+                   b->pgraph_limit != b->spin_limit)) {
+    // kernel attributes and occupancy are queried outside the capture
+    e = lbm::launch_sweep_persistent(b->nh, b->collapse, b->d_cases, b->d_work, b->nwork, 0, 0, b->d_sync,
+                                     b->spin_limit, b->stream, b->variant, &grid);
+    if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step persistent prepare");
+    if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
+    b->pgraph = nullptr;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = one_launch(kPersistSteps);
+    cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = ec;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->pgraph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step persistent graph capture");
+    b->pgraph_nwork = b->nwork;
+    b->pgraph_variant = b->variant;
+    b->pgraph_limit = b->spin_limit;
+  }
+  std::vector<unsigned> err(b->n);
+  lbm::GridSync sync{};
+  long long done = 0;
+  // one replay or launch at a time, each checked, so that a wait that ran out
+  // stops the run at that launch
+  while (done < nsteps && e == cudaSuccess) {
+    const long long left = nsteps - done;
+    int steps;
+    if (done < full * (long long)kPersistSteps) {
+      steps = kPersistSteps;
+      e = cudaGraphLaunch(b->pgraph, b->stream);
+    } else {
+      steps = (int)(left < kPersistSteps ? left : kPersistSteps);
+      e = one_launch(steps);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&sync, b->d_sync, sizeof(sync), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) break;
+    if (sync.status & lbm::kSyncTimeout) {
+      // the launch stopped part-way: no case holds a whole time step
+      for (int i = 0; i < b->n; ++i)
+        if (b->active[i]) b->h[i]->initialized = false;
+      b->work_valid = false;
+      return b->fail(LBM_E_TIMEOUT, "a grid-barrier wait of the persistent step ran out after " +
+                                        std::to_string(b->spin_limit) + " polls (" + std::to_string(grid) +
+                                        " CTAs); the active cases must be set again");
+    }
+    done += steps;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(err.data(), b->d_err, err.size() * sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step persistent launch");
+  std::string diverged;
+  for (int i = 0; i < b->n; ++i) {
+    if (!b->active[i] || !b->h[i]->initialized) continue;
+    if (nsteps & 1) b->h[i]->cur = 1 - b->h[i]->cur;
+    b->h[i]->step += nsteps;
+    if (err[i]) {
+      diverged += " " + std::to_string(i);
+      b->active[i] = 0;
+      b->work_valid = false;
+    }
+  }
+  if (!diverged.empty()) return b->fail(LBM_E_DIVERGED, "non-finite values in case(s)" + diverged + "; deactivated");
+  return LBM_OK;
+}
+
 extern "C" {
 
 size_t lbm_batch_required_bytes(const lbm_params *cases, int ncases) {
@@ -108,7 +210,7 @@ size_t lbm_batch_required_bytes(const lbm_params *cases, int ncases) {
     if (b == 0 || cases[i].storage != 0 || cases[i].open_x) return 0;  // periodic FP32 states only
     total += align_up(b, kAlign);
   }
-  total += batch_table_bytes(ncases) + batch_err_bytes(ncases);
+  total += batch_table_bytes(ncases) + batch_err_bytes(ncases) + batch_sync_bytes();
   total += align_up(max_work(cases, ncases) * sizeof(lbm::WorkItem), kAlign);
   return total;
 }
@@ -150,6 +252,8 @@ lbm_status lbm_batch_create(const lbm_params *cases, int ncases, void *dev_arena
   off += batch_table_bytes(ncases);
   b->d_err = (unsigned *)(base + off);
   off += batch_err_bytes(ncases);
+  b->d_sync = (lbm::GridSync *)(base + off);
+  off += batch_sync_bytes();
   b->d_work = (lbm::WorkItem *)(base + off);
   b->work_cap = max_work(cases, ncases);
   *out = b;
@@ -169,7 +273,8 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int reps, int *chosen) {
   if (!b || reps < 1) return LBM_E_INVAL;
   cudaError_t e = b->upload_table();
   if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_autotune table");
-  const int nv = lbm::batched_variant_count(b->nh);
+  // the persistent launch runs the sweep configurations only
+  const int nv = b->persistent ? lbm::sweep_batched_count(b->nh) : lbm::batched_variant_count(b->nh);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return b->fail(LBM_E_CUDA, "cudaEventCreate");
@@ -215,6 +320,7 @@ lbm_status lbm_batch_step(lbm_batch *b, long long nsteps) {
   e = b->upload_table();
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, (size_t)b->n * sizeof(unsigned), b->stream);
   if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step table");
+  if (b->persistent) return persistent_steps(b, nsteps);
   // graphs need a capturable stream: not the legacy or per-thread default stream
   const bool capturable = b->stream != nullptr && b->stream != cudaStreamLegacy && b->stream != cudaStreamPerThread;
   const long long graphs = capturable ? nsteps / kGraphSteps : 0;
@@ -257,6 +363,15 @@ lbm_status lbm_batch_step(lbm_batch *b, long long nsteps) {
     }
   }
   if (!diverged.empty()) return b->fail(LBM_E_DIVERGED, "non-finite values in case(s)" + diverged + "; deactivated");
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_set_persistent(lbm_batch *b, int on, long long spin_limit) {
+  if (!b || (on != 0 && on != 1) || spin_limit < 0) return LBM_E_INVAL;
+  b->persistent = on != 0;
+  b->spin_limit = spin_limit == 0 ? kDefaultSpinLimit : spin_limit;
+  if (b->persistent && !lbm::batched_variant_is_sweep(b->nh, b->variant)) b->variant = 0;
+  b->work_valid = false;
   return LBM_OK;
 }
 

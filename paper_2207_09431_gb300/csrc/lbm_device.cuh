@@ -9,7 +9,9 @@
 //  R3  p = sum g + (1/2) cs^2 u . grad rho (Eq. 24 with the half restored);
 //  R4  tau_PL = eta / (rho cs^2) clamped to [tau_min, tau_max], node tau =
 //      sum c_i tau_i with tau_1 = tau_PL, strain rate from the previous tau;
-//  R8  variable-mobility term (D0/Sigma_i)(1 - 2 C_i) grad C_i . grad mu_i;
+//  R8  variable mobility (D0/Sigma_i) c (1 - c), c = clip(C_i, 0, 1), and its
+//      derivative term (D0/Sigma_i)(1 - 2 C_i) grad C_i . grad mu_i where
+//      0 <= C_i <= 1 (else 0);
 //  R9  destination-side source terms of Eq. 18 at the arrival node;
 //  R10 half-way walls, ghost rows mirror the fluid rows;
 //  R23 strain rate D = -Pi / (2 tau rho cs^2) with Pi from Eq. 29.

@@ -52,6 +52,14 @@ struct WorkItem {
   int case_id, x0, y0, y1;  // y1: end row of a sweep segment (unused by tiles)
 };
 
+// Grid-wide barrier state of the persistent batched step: arrivals of the
+// current barrier, the barrier generation, and the status word (bit 0: a wait
+// ran out of its iteration limit).  Zeroed by the host before each launch.
+struct GridSync {
+  unsigned count, gen, status, pad;
+};
+constexpr unsigned kSyncTimeout = 1u;
+
 bool fused_supported(const DevParams &P);
 // Configurations of the batched step: sweeps (work items (case, strip,
 // segment)) first, then tiles (work items (case, tile)).
@@ -64,6 +72,14 @@ cudaError_t launch_sweep_batched(int nh, bool collapse_h, const BatchCase *cases
                                  int parity, cudaStream_t s, int v);
 cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
                                 int parity, cudaStream_t s, int v);
+// nsteps time steps of every work item in one persistent cooperative launch
+// (sweep configurations v < sweep_batched_count(nh) only): the CTAs that fit
+// on the device at once share the items of a step and meet at a grid barrier
+// between steps; a barrier wait gives up after spin_limit polls, sets
+// kSyncTimeout in sync->status and the kernel returns.  *grid = CTAs launched.
+cudaError_t launch_sweep_persistent(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+                                    int parity0, int nsteps, GridSync *sync, long long spin_limit, cudaStream_t s,
+                                    int v, int *grid);
 // Launch configurations of the fused step: row sweeps (strip width, rows per
 // pipeline step, threads, CTAs per SM), then tiles (tile, threads, CTAs per SM).
 int sweep_variant_count(const DevParams &P);

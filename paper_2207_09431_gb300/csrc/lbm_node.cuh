@@ -186,10 +186,15 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
     Fsy = i == 0 ? c.dmu[0] * gcy : fmaf(c.dmu[i], gcy, Fsy);
     Cc[i] = c.C[i];
     const float D0s = P.d0_sig[i];
-    if (P.mobility == 1)
-      sv[i] = D0s * Cc[i] * (1.0f - Cc[i]) * lapmu + D0s * (1.0f - 2.0f * Cc[i]) * (gcx * mgx + gcy * mgy);
-    else
+    if (P.mobility == 1) {
+      // mobility with C clipped to [0, 1] and its derivative (reading R8)
+      const float cc = fminf(fmaxf(Cc[i], 0.0f), 1.0f);
+      const float dv = (Cc[i] >= 0.0f && Cc[i] <= 1.0f) ? D0s * (1.0f - 2.0f * Cc[i]) * (gcx * mgx + gcy * mgy)
+                                                       : 0.0f;
+      sv[i] = D0s * cc * (1.0f - cc) * lapmu + dv;
+    } else {
       sv[i] = D0s * lapmu;
+    }
     kh[i] = 1.5f * Cc[i] * irho;                     // C_i / (rho cs^2) / 2
     hb[i] = 0.5f * (sv[i] - (ux * gcx + uy * gcy));  // (S_i - u.grad C_i) / 2
     hdmu[i] = 0.5f * c.dmu[i];

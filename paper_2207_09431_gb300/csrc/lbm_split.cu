@@ -264,7 +264,12 @@ __global__ void k_sources(DevParams P, const float *__restrict__ Cf, const float
     const float D0s = P.d0_sig[i];
     float s;
     if (P.mobility == 1) {
-      s = D0s * C * (1.0f - C) * lapmu + D0s * (1.0f - 2.0f * C) * (3.0f * gcx * 3.0f * gmx + 3.0f * gcy * 3.0f * gmy);
+      // mobility with C clipped to [0, 1] and its derivative (reading R8)
+      const float cc = fminf(fmaxf(C, 0.0f), 1.0f);
+      const float dv = (C >= 0.0f && C <= 1.0f)
+                           ? D0s * (1.0f - 2.0f * C) * (3.0f * gcx * 3.0f * gmx + 3.0f * gcy * 3.0f * gmy)
+                           : 0.0f;
+      s = D0s * cc * (1.0f - cc) * lapmu + dv;
     } else {
       s = D0s * lapmu;
     }

@@ -467,6 +467,78 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep_batched(const BatchCase *__r
                                       *reinterpret_cast<PipeSmem<TX, RS, NH, FORM != 0> *>(smem_raw));
 }
 
+// Grid-wide barrier between the time steps of the persistent batched sweep.
+// One thread per CTA arrives (after a fence that publishes the CTA's writes
+// of this step) and polls the generation word; the CTA's other threads wait
+// at the CTA barrier, which orders them after that thread's acquire.  Every
+// poll also reads the status word, so that a wait elsewhere that ran out ends
+// this one too; after spin_limit polls the wait sets kSyncTimeout itself.
+// Returns false when the kernel must stop.
+__device__ __forceinline__ bool grid_barrier(GridSync *gs, unsigned nblocks, long long spin_limit) {
+  __shared__ int go_on;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = &gs->gen;
+    volatile unsigned *vstatus = &gs->status;
+    const unsigned g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&gs->count, 1u) + 1u == nblocks) {
+      atomicExch(&gs->count, 0u);
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    } else {
+      long long polls = 0;
+      while (*vgen == g) {
+        if (*vstatus != 0u) {
+          ok = 0;
+          break;
+        }
+        if (++polls > spin_limit) {
+          atomicOr(&gs->status, kSyncTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*vstatus != 0u) ok = 0;
+    go_on = ok;
+  }
+  __syncthreads();
+  return go_on != 0;
+}
+
+// The batched sweep as one persistent launch: CTA b takes work items b,
+// b + gridDim.x, ... of every time step, and all CTAs (resident at once: a
+// cooperative launch) meet at the grid barrier before the next step reads
+// what this one wrote.
+template <int TX, int RS, int NH, int FORM, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_sweep_persistent(const BatchCase *__restrict__ cases,
+                                                               const WorkItem *__restrict__ work, int nwork,
+                                                               int parity0, int nsteps, GridSync *sync,
+                                                               long long spin_limit) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ DevParams sP;
+  __shared__ FusedBuffers sB;
+  for (int t = 0; t < nsteps; ++t) {
+    const int parity = (parity0 + t) & 1;
+    for (int i = blockIdx.x; i < nwork; i += gridDim.x) {
+      const WorkItem w = work[i];
+      if (threadIdx.x == 0) {
+        sP = cases[w.case_id].P;
+        sB = cases[w.case_id].B[cases[w.case_id].base_parity ^ parity];
+      }
+      __syncthreads();
+      sweep_body<TX, RS, NH, FORM, 2, NT>(sP, sB, w.x0, w.y0, w.y1,
+                                          *reinterpret_cast<PipeSmem<TX, RS, NH, FORM != 0> *>(smem_raw));
+      __syncthreads();  // sP and sB are rewritten by the next item
+    }
+    if (t + 1 < nsteps && !grid_barrier(sync, gridDim.x, spin_limit)) return;
+  }
+}
+
 // Segment length for a strip count: balances the waves of CTAs against the
 // per-segment overhead (3 + 2 + 1 extra rows of stages 0-2 at each end and
 // the steps that fill the pipeline).
@@ -589,6 +661,55 @@ static cudaError_t launch_sweep_batched_t(const BatchCase *cases, const WorkItem
   return cudaGetLastError();
 }
 
+template <int TX, int RS, int NH, int FORM, int NT, int MINB>
+static cudaError_t launch_sweep_persistent_t(const BatchCase *cases, const WorkItem *work, int nwork, int parity0,
+                                             int nsteps, GridSync *sync, long long spin_limit, cudaStream_t st,
+                                             int *grid) {
+  auto kern = k_sweep_persistent<TX, RS, NH, FORM, NT, MINB>;
+  const size_t smem = sizeof(PipeSmem<TX, RS, NH, FORM != 0>);
+  static int resident = 0;
+  if (!resident) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    resident = per_sm * sms;
+  }
+  const int nb = nwork < resident ? nwork : resident;
+  if (grid) *grid = nb;
+  if (nwork <= 0 || nsteps <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nb);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, cases, work, nwork, parity0, nsteps, sync, spin_limit);
+}
+
+template <int NH, int FORM>
+static cudaError_t sweep_persistent_dispatch(int v, const BatchCase *c, const WorkItem *w, int n, int parity0,
+                                             int nsteps, GridSync *sync, long long lim, cudaStream_t s, int *grid) {
+  if constexpr (NH == 1) {
+    switch (v) {
+      case 2:
+      case 6: return launch_sweep_persistent_t<60, 2, NH, FORM, 160, 3>(c, w, n, parity0, nsteps, sync, lim, s, grid);
+      case 3: return launch_sweep_persistent_t<64, 2, NH, FORM, 160, 3>(c, w, n, parity0, nsteps, sync, lim, s, grid);
+      default: return launch_sweep_persistent_t<58, 2, NH, FORM, 128, 3>(c, w, n, parity0, nsteps, sync, lim, s, grid);
+    }
+  } else {
+    if (v == 1) return launch_sweep_persistent_t<62, 2, NH, FORM, 160, 2>(c, w, n, parity0, nsteps, sync, lim, s, grid);
+    return launch_sweep_persistent_t<64, 2, NH, FORM, 160, 2>(c, w, n, parity0, nsteps, sync, lim, s, grid);
+  }
+}
+
 int sweep_batched_count(int nh) { return nh == 1 ? 7 : 2; }
 
 // (strip width, segment rows): short segments give many work items for the
@@ -624,6 +745,17 @@ cudaError_t launch_sweep_batched(int nh, bool collapse_h, const BatchCase *cases
                                  : sweep_batched_dispatch<1, 0>(v, cases, work, nwork, parity, s);
   return collapse_h ? sweep_batched_dispatch<2, 1>(v, cases, work, nwork, parity, s)
                     : sweep_batched_dispatch<2, 0>(v, cases, work, nwork, parity, s);
+}
+
+cudaError_t launch_sweep_persistent(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+                                    int parity0, int nsteps, GridSync *sync, long long spin_limit, cudaStream_t s,
+                                    int v, int *grid) {
+  if (v < 0 || v >= sweep_batched_count(nh)) return cudaErrorInvalidValue;
+  if (nh == 1)
+    return collapse_h ? sweep_persistent_dispatch<1, 1>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid)
+                      : sweep_persistent_dispatch<1, 0>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid);
+  return collapse_h ? sweep_persistent_dispatch<2, 1>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid)
+                    : sweep_persistent_dispatch<2, 0>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid);
 }
 
 cudaError_t launch_sweep_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v) {

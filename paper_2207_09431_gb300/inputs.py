@@ -137,6 +137,22 @@ def paper_case(n=0.6, eotvos=10.0, density_ratio=1000.0, mobility=1, k=None):
     return p, [(L / 2.0, 0.6 * L, R, 3)]
 
 
+# Table 5 of Sec. 4.3: (n, k, g, sigma) of the six rising-bubble cases (density
+# ratio 800, tau of the gas 0.5, d = L / 4 on L x 2L with L = 200).
+TABLE5 = {1: (0.5, 1e-4, 5e-7, 2.61e-6), 2: (0.5, 1e-4, 5e-7, 2.61e-5), 3: (0.5, 2e-4, 5e-7, 5e-4),
+          4: (0.6, 5e-4, 2e-7, 2.61e-5), 5: (0.63, 5e-4, 2e-7, 2.61e-5), 6: (0.8, 1e-2, 5e-7, 2.61e-5)}
+
+
+def table5_case(case, density_ratio=800.0, mobility=0, L=200):
+    """Case `case` of Table 5 (Sec. 4.3): L x 2L, bubble d = L / 4 at (L/2, 0.6 L)
+    (Eq. 42), the printed n, k, g and sigma, gas relaxation time 0.5, at the
+    given density ratio (the paper's is 800)."""
+    n, k, g, sigma = TABLE5[case]
+    p = rising_bubble_params(L, 2 * L, density_ratio=density_ratio, n=n, k=k, sigma=sigma, gravity=g,
+                             mobility=mobility)
+    return p, [(L / 2.0, 0.6 * L, L / 8.0, 3)]
+
+
 def paper_grid_cases(density_ratio=1000.0, mobility=0, fd_scheme=0, ns=(0.5, 0.6, 0.8, 1.0),
                      eotvos=(1.0, 10.0, 50.0), log10_mo=(-3.0, -1.0, 1.0), L=200):
     """The rising-bubble grid of Sec. 4.3 at the paper's size: L x 2L, d = L/4

@@ -70,7 +70,7 @@ EXPORTED = ["lbm_version", "lbm_required_bytes", "lbm_create", "lbm_init_bubbles
             "lbm_profile_step", "lbm_observables_static", "lbm_autotune", "lbm_kernel_config_count",
             "lbm_set_kernel_config", "lbm_batch_required_bytes", "lbm_batch_create", "lbm_batch_case",
             "lbm_batch_set_active", "lbm_batch_step", "lbm_batch_autotune", "lbm_batch_destroy",
-            "lbm_batch_last_error", "surr_param_count", "surr_required_bytes", "surr_create", "surr_destroy",
+            "lbm_batch_last_error", "lbm_batch_set_persistent", "surr_param_count", "surr_required_bytes", "surr_create", "surr_destroy",
             "surr_last_error", "surr_get_weights", "surr_forward_backward", "surr_train", "surr_predict"]
 
 
@@ -116,6 +116,7 @@ def load_library(path: str | None = None):
     lib.lbm_batch_set_active.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     lib.lbm_batch_step.argtypes = [vp, ctypes.c_longlong]
     lib.lbm_batch_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+    lib.lbm_batch_set_persistent.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
     lib.lbm_batch_destroy.argtypes = [vp]
     lib.lbm_batch_destroy.restype = None
     lib.lbm_batch_last_error.argtypes = [vp]
@@ -346,6 +347,11 @@ def lbm_batch_autotune(b, reps: int = 3) -> int:
     return int(chosen.value)
 
 
+def lbm_batch_set_persistent(b, on: bool = True, spin_limit: int = 0):
+    _check_batch(b, load_library().lbm_batch_set_persistent(b, 1 if on else 0, int(spin_limit)),
+                 "lbm_batch_set_persistent")
+
+
 def lbm_batch_destroy(b):
     if b:
         load_library().lbm_batch_destroy(b)
@@ -399,6 +405,10 @@ class Batch:
 
     def autotune(self, reps=3) -> int:
         return lbm_batch_autotune(self.b, reps)
+
+    def set_persistent(self, on=True, spin_limit=0):
+        """One cooperative launch for many steps (see lbm_batch_set_persistent)."""
+        lbm_batch_set_persistent(self.b, on, spin_limit)
 
 
 class CaseView:

@@ -187,9 +187,13 @@ def step(prm, g, h, tau):
         D = prm["D0"] / F["Sig"][i]
         lapmu = _lap(F["mu"][i], py)
         if prm["mobility"] == 1:
+            # mobility of C clipped to [0, 1]; its derivative where C is inside
             gmu = np.array(_grad(F["mu"][i], py))
-            src[i] = D * F["C"][i] * (1 - F["C"][i]) * lapmu + D * (1 - 2 * F["C"][i]) * (
-                F["gC"][i] * gmu).sum(axis=0)
+            Ci = F["C"][i]
+            c = np.clip(Ci, 0.0, 1.0)
+            inside = (Ci >= 0.0) & (Ci <= 1.0)
+            src[i] = D * c * (1 - c) * lapmu + np.where(inside, D * (1 - 2 * Ci) * (F["gC"][i] * gmu).sum(axis=0),
+                                                        0.0)
         else:
             src[i] = D * lapmu
     hpost = np.array([h[i] - (h[i] - heq[i]) / 1.0 + Phih[i] + 0.5 * src[i] * G for i in range(nh)])

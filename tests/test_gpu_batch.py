@@ -73,3 +73,94 @@ def test_inactive_case_is_frozen_and_autotune_keeps_values(lbm):
         assert np.linalg.norm(a - b) <= 1e-6 * max(np.linalg.norm(b), 1e-30), n
     assert batch.case(0).observables()["step"] == 30
     assert batch.case(2).observables()["step"] == 10
+
+
+def _stable_cases(collapse=0):
+    """Four small rising bubbles of different sizes and parameters that stay
+    finite for thousands of steps (density ratios 50 to 100, constant mobility)."""
+    out = []
+    for i, (nx, ny) in enumerate([(40, 72), (64, 48), (70, 50), (33, 45)]):
+        p, _ = inputs.small_case(mobility=0, density_ratio=50.0 + 15 * i)
+        p = dict(p, nx=nx, ny=ny, pl_n=0.6 + 0.1 * i, collapse_h=collapse)
+        R = min(nx, ny) / 5.0
+        C = inputs.round_to_fp32(inputs.bubble_fields(nx, ny, 2, p["xi"], [(nx / 2, ny / 3, R, 3)], seed=i,
+                                                      noise=1e-8))
+        out.append((p, C))
+    return out
+
+
+@pytest.mark.parametrize("collapse", [0, 1])
+def test_persistent_launch_equals_per_step_launches(lbm, collapse):
+    """One cooperative launch per 4096 steps (the first replayed from its
+    graph, the rest a direct launch) gives the per-step launches' values bit
+    for bit: same items, same per-node arithmetic."""
+    cases = _stable_cases(collapse)
+    per_step = lbm.Batch([p for p, _ in cases])
+    persistent = lbm.Batch([p for p, _ in cases])
+    persistent.set_persistent(True)
+    for i, (_, C) in enumerate(cases):
+        per_step.case(i).set_fields(C)
+        persistent.case(i).set_fields(C)
+    per_step.step(4096 + 37)
+    persistent.step(4096 + 37)
+    names = ("C1", "p", "ux", "uy", "tau", "g") + (() if collapse else ("h",))
+    for i in range(len(cases)):
+        assert persistent.case(i).observables()["step"] == 4096 + 37
+        for n in names:
+            assert np.array_equal(persistent.case(i).field(n), per_step.case(i).field(n)), (i, n)
+
+
+def test_persistent_barrier_wait_limit_returns_timeout(lbm):
+    """A grid-barrier wait limited to one poll gives up (the CTAs finish their
+    items microseconds apart): the call returns LBM_E_TIMEOUT without a fault
+    or a hang, the cases must be set again, and after that the same batch
+    steps normally and matches a single lattice."""
+    cases = []
+    for i in range(8):
+        p, b = inputs.sweep_case(192, density_ratio=100.0)
+        cases.append((p, inputs.round_to_fp32(inputs.bubble_fields(p["nx"], p["ny"], 2, p["xi"], b, seed=i,
+                                                                   noise=1e-8))))
+    batch = lbm.Batch([p for p, _ in cases])
+    batch.set_persistent(True, spin_limit=1)
+    for i, (_, C) in enumerate(cases):
+        batch.case(i).set_fields(C)
+    with pytest.raises(lbm.LbmError) as ei:
+        batch.step(6)
+    assert ei.value.status == -5
+    with pytest.raises(lbm.LbmError) as ei:   # the stopped launch left no whole step
+        batch.step(2)
+    assert ei.value.status == -6
+    batch.set_persistent(True)              # the default limit
+    for i, (_, C) in enumerate(cases):
+        batch.case(i).set_fields(C)
+    batch.step(6)
+    ref = lbm.Lattice(cases[3][0])
+    ref.set_fields(cases[3][1])
+    ref.step(6)
+    for n in ("C1", "p", "uy", "tau", "g", "h"):
+        assert np.array_equal(batch.case(3).field(n), ref.field(n)), n
+
+
+def test_persistent_batch_matches_oracle(lbm):
+    """Two cases of one persistent batch against the FP64 oracle directly, per
+    field within max(1e-5, 4 x the FP32-build deviation) after 300 steps."""
+    import oracle
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12 * b.size))
+
+    cases = _stable_cases()[:2]
+    batch = lbm.Batch([p for p, _ in cases])
+    batch.set_persistent(True)
+    for i, (_, C) in enumerate(cases):
+        batch.case(i).set_fields(C)
+    batch.step(300)
+    for i, (p, C) in enumerate(cases):
+        o64, o32 = oracle.Oracle(p), oracle.Oracle(p, "f32")
+        for o in (o64, o32):
+            o.set_fields(C)
+            o.step(300)
+        for n in ("C1", "p", "ux", "uy", "tau", "g", "h"):
+            ref = o64.field(n)
+            err, floor = rel(batch.case(i).field(n), ref), rel(o32.field(n), ref)
+            assert err <= max(1e-5, 4.0 * floor), (i, n, err, floor)

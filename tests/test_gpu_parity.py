@@ -11,8 +11,11 @@ p, u and g, 2e-4 on tau.  The floor comes from FP32 arithmetic, not storage
 6e-8, the chemical potential is a near-cancellation of the double-well and
 Laplacian terms, and the gas velocity divides by rho_gas.  So for each field
 the CUDA path must match the FP64 oracle in relative L2 (denominator
-max(||ref||, 1e-12 N)) within max(1e-5, 4 x floor), the floor measured live on
-the same case with the FP32 build.
+max(||ref||, 1e-12 N)) within max(1e-5, 3 x floor), the floor measured live on
+the same case with the FP32 build (measured ratios err / floor: at most 2.5,
+most below 1).  The collapsed state form (C stored instead of h) computes the
+same step in another order of operations than the population form the FP32
+build follows; its bound is 4 x floor (measured ratio up to 3.0).
 """
 import numpy as np
 import pytest
@@ -24,7 +27,8 @@ from paper_2207_09431_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-FLOOR_FACTOR = 4.0
+FLOOR_FACTOR = 3.0
+COLLAPSED_FACTOR = 4.0
 STATE = ("C1", "p", "ux", "uy", "tau", "g", "h")
 
 
@@ -70,7 +74,8 @@ class Case:
             report[name] = (err, floor)
             if not err <= tol:
                 bad[name] = (err, tol)
-        print("parity (gpu err, fp32 floor):", {k: f"{e:.1e}/{f:.1e}" for k, (e, f) in report.items()})
+        print("parity (gpu err, fp32 floor, ratio):",
+              {k: f"{e:.1e}/{f:.1e}/{e / max(f, 1e-30):.2f}" for k, (e, f) in report.items()})
         assert not bad, f"parity failures {bad}"
         return report
 
@@ -151,8 +156,9 @@ def test_small_rising_bubble_1000_steps(lbm):
         assert abs(og["mass"][i] - oo["mass"][i]) / oo["mass"][i] <= max(1e-6, FLOOR_FACTOR * floor)
 
 
-def test_three_components_periodic(lbm):
-    p, b = inputs.three_comp_case(nx=64, mobility=0, seed=3)
+@pytest.mark.parametrize("mobility", [0, 1])
+def test_three_components_periodic(lbm, mobility):
+    p, b = inputs.three_comp_case(nx=64, mobility=mobility, seed=3)
     C = inputs.round_to_fp32(inputs.bubble_fields(64, 64, 3, p["xi"], b, seed=3, noise=1e-8, periodic_y=True))
     c = Case(lbm, p, C)
     c.step(200)
@@ -218,7 +224,7 @@ def test_collapsed_state_form(lbm, mobility):
     p, C = _bubble_case(56, 90, mobility=mobility)
     c = Case(lbm, p, C, gpu_params=dict(p, collapse_h=1))
     c.step(300)
-    c.check(names=("C1", "p", "ux", "uy", "tau", "g"))
+    c.check(names=("C1", "p", "ux", "uy", "tau", "g"), factor=COLLAPSED_FACTOR)
     with pytest.raises(lbm.LbmError):
         c.lat.field("h")
 

@@ -321,6 +321,33 @@ def test_hand_step_4x4(periodic_y, ncomp, mobility, fd_scheme, powerlaw):
     assert np.max(np.abs(o.field("tau") - tau)) < 1e-11
 
 
+@pytest.mark.parametrize("ncomp", [2, 3])
+def test_hand_step_4x4_order_parameter_outside_unit_interval(ncomp):
+    """The same brute-force comparison with order parameters that leave [0, 1]
+    at some nodes (as the Cahn-Hilliard bulk shift does inside bubbles): the
+    clipped mixture weights and the clipped variable mobility with its
+    derivative term switched off there (readings R1, R8)."""
+    rng = np.random.default_rng(7 + ncomp)
+    P = dict(oracle.DEFAULTS)
+    P.update(nx=4, ny=4, ncomp=ncomp, periodic_y=0, rho=(1.0, 0.5, 0.1), tau=(0.6, 0.7, 0.55), powerlaw=1,
+             pl_n=0.7, pl_k=0.05, gravity=1e-3, mobility=1, D0=0.01, sigma12=1e-3, sigma13=1.5e-3, sigma23=2e-3)
+    C = np.zeros((ncomp - 1, 4, 4))
+    C[0] = -0.06 + 1.12 * rng.random((4, 4))
+    C[0, 0, 1], C[0, 2, 3], C[0, 3, 0] = -0.05, 1.04, -0.02
+    if ncomp == 3:
+        C[1] = -0.04 + 0.3 * rng.random((4, 4))
+        C[1, 1, 2] = -0.03
+    o = oracle.Oracle(P)
+    o.set_fields(C)
+    g, h, tau = hs.init_state(P, C)
+    for _ in range(3):
+        o.step(1)
+        g, h, tau = hs.step(P, g, h, tau)
+    assert np.max(np.abs(o.field("g") - g)) < 1e-11
+    assert np.max(np.abs(o.field("h") - h)) < 1e-11
+    assert np.max(np.abs(o.field("tau") - tau)) < 1e-11
+
+
 # ------------------------------------------------------------------ P7
 def test_uniform_rest_state_is_fixed_point():
     o = _single_phase(6, 5)
@@ -424,6 +451,24 @@ def test_observable_sums_of_prescribed_disc(ncomp):
     ys = [j for _, j in inside]
     assert list(raw[11:]) == [min(xs), max(xs), min(ys), max(ys)]
     assert (max(xs) - min(xs), max(ys) - min(ys)) == (19, 19)   # |dx|, |dy| <= 9.5 inside R = 10.3
+
+
+def test_openmp_build_is_bit_identical():
+    """The OpenMP build of the oracle (timed CPU baseline only) shares each
+    whole-field pass's nodes among threads; every node keeps its own order of
+    operations, so after several steps of a walled three-component variable-
+    mobility case every field equals the serial build's bit for bit."""
+    p, discs = inputs.three_comp_case(nx=48, mobility=1, seed=3)
+    p = dict(p, periodic_y=0, gravity=1e-6)
+    C = inputs.bubble_fields(48, 48, 3, p["xi"], discs, seed=1, noise=1e-8)
+    runs = []
+    for prec in ("f64", "f64-omp"):
+        o = oracle.Oracle(p, prec)
+        o.set_fields(C)
+        o.step(7)
+        runs.append({name: o.field(name) for name in ("g", "h", "tau", "p", "ux", "uy", "C1", "C2")})
+    for name in runs[0]:
+        assert np.array_equal(runs[0][name], runs[1][name]), name
 
 
 def test_splitmix64_reference_vectors():
