@@ -163,7 +163,13 @@ lbm_status lbm_set_fields(lbm_handle *h, const double *C, const double *p, const
                           const double *uy);
 
 /* Enqueues nsteps time steps (Sec. 2.2-2.3) on the handle's stream and waits
- * for them; returns LBM_E_DIVERGED if a non-finite value appeared. */
+ * for them; returns LBM_E_DIVERGED if a non-finite value appeared.  Exception
+ * to the rule that a failed call leaves the prior state: after LBM_E_DIVERGED
+ * the handle holds the state of all nsteps steps (with its non-finite values,
+ * for inspection through lbm_get_field) and its step count has advanced; a
+ * checkpoint (lbm_load) or new fields restore a valid state.  The library does
+ * not keep a copy of the previous state, which would double the device memory
+ * and the traffic of every call. */
 lbm_status lbm_step(lbm_handle *h, long long nsteps);
 
 /* Computes the observables of the current state (FP64 sums on the device,
@@ -221,8 +227,9 @@ lbm_status lbm_postprocess(const lbm_params *p, const double raw[15], lbm_obs *o
  * (a work list of (case, tile) items), and runs of 16 steps are replayed from a
  * captured CUDA graph (on a created stream; on the legacy or per-thread default
  * stream the steps are launched directly); or, in persistent mode
- * (lbm_batch_set_persistent), one launch covers thousands of steps.  All cases share ncomp and collapse_h and use
- * fd_scheme 0 and storage 0.  Each case is an ordinary handle carved from the batch arena:
+ * (lbm_batch_set_persistent), one launch covers thousands of steps.  All cases
+ * share ncomp, collapse_h and storage (FP32, or FP16 g with collapse_h 1) and
+ * use fd_scheme 0.  Each case is an ordinary handle carved from the batch arena:
  * set its initial state, read its observables, fields and checkpoints with the
  * single-lattice calls on lbm_batch_case(b, i); lbm_step on a case advances that
  * case alone.  The arena (>= lbm_batch_required_bytes) and the stream stay the
@@ -259,6 +266,35 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int reps, int *chosen);
  * is stepped.  This mode extends the paper's method to ensembles (Sec. 4.3 runs
  * its cases one by one). */
 lbm_status lbm_batch_set_persistent(lbm_batch *b, int on, long long spin_limit);
+/* Terminal state of a rising bubble (reading of Sec. 4.2-4.3, which gives no
+ * criterion): the rise velocity averaged over windows of `window` steps, i.e.
+ * the centroid displacement of Eq. 44 over the window divided by its length,
+ * changes by less than rtol of itself between two consecutive pairs of
+ * windows.  A case also stops when its centroid comes within top_margin
+ * area-equivalent diameters (its initial d, Eq. 38) of the top row, or after
+ * max_steps steps. */
+typedef struct {
+  long long window;    /* steps per window (> 0) */
+  double rtol;         /* relative change between consecutive windows (> 0) */
+  long long max_steps; /* steps after which a case stops unconverged (>= window) */
+  double top_margin;   /* in initial diameters below the top row (>= 0) */
+} lbm_run_opts;
+
+/* Outcome of one case of lbm_batch_run. */
+enum { LBM_RUN_MAX_STEPS = 0, LBM_RUN_TERMINAL = 1, LBM_RUN_TOP = 2, LBM_RUN_DIVERGED = -1, LBM_RUN_SKIPPED = -2 };
+
+/* Runs every active, initialised case of the batch to its terminal state (the
+ * cases advance together with lbm_batch_step, in the batch's current launch
+ * mode, one window at a time; a case leaves the batch when it stops).  For
+ * case i: outcome[i] is one of LBM_RUN_*, steps[i] (may be NULL) the steps it
+ * ran, and out[i] its observables at the stop, with rise_velocity = U_t, the
+ * window-averaged rise velocity of its last window (0 before a whole window),
+ * and drag_coefficient, Re and Mo recomputed from U_t (Eq. 37-40); cases that
+ * were inactive or uninitialised get LBM_RUN_SKIPPED and are left unchanged.
+ * Cases that stopped stay inactive.  Returns LBM_E_INVAL for bad options,
+ * LBM_E_TIMEOUT / LBM_E_CUDA as lbm_batch_step; a diverged case is an outcome,
+ * not an error. */
+lbm_status lbm_batch_run(lbm_batch *b, const lbm_run_opts *opts, lbm_obs *out, int *outcome, long long *steps);
 void lbm_batch_destroy(lbm_batch *b);
 const char *lbm_batch_last_error(const lbm_batch *b);
 
@@ -298,6 +334,24 @@ lbm_status surr_train(surr_net *n, const double *X, const double *Y, int rows, i
  * the mean) of the two outputs for rows x 5 raw inputs; outside[r] = 1 when
  * input r lies outside the training box.  y_spread and outside may be NULL. */
 lbm_status surr_predict(surr_net *n, const double *X, int rows, double *y_mean, double *y_spread, int *outside);
+/* Terminal rise velocity and drag coefficient (Sec. 4.3, Eq. 37) of `rows`
+ * rising-bubble cases, from the network where the case is trusted and from the
+ * lattice Boltzmann solver (the fallback) elsewhere.  Trusted: the features
+ * X[r] (rows x 5, as for surr_predict) lie inside the training box and every
+ * member lies within max_spread of the ensemble mean in both outputs, which are
+ * (log U_t, log C_D) as the caller trained them.  The untrusted cases are set
+ * up from cases[r] and bubbles[r] (one disc each; lbm_init_bubbles with seed r
+ * and noise_amp), advanced together as one batch carved from dev_arena (at
+ * least lbm_batch_required_bytes of those cases; every case must suit a batch)
+ * on the network's stream, and run to their terminal state by lbm_batch_run
+ * with opts.  y_out: rows x 2 (U_t, C_D), NaN where a fallback case diverged;
+ * used_fallback[r] = 1 where the solver answered; fallback_outcome (may be
+ * NULL) receives the LBM_RUN_* outcome of each solved case and LBM_RUN_SKIPPED
+ * for the others.  The paper has no surrogate (it serves the parameter studies
+ * of Sec. 4.3).  Returns LBM_E_NOMEM if the arena is too small. */
+lbm_status surr_answer(surr_net *n, const double *X, const lbm_params *cases, const lbm_bubble *bubbles, int rows,
+                       double max_spread, double noise_amp, const lbm_run_opts *opts, void *dev_arena,
+                       size_t arena_bytes, double *y_out, int *used_fallback, int *fallback_outcome);
 
 /* Largest lattice (nx * ny nodes) lbm_observables_static accepts. */
 #define LBM_STATIC_MAX_NODES (1 << 20)

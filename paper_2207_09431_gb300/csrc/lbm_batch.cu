@@ -8,6 +8,7 @@
 // use the single-lattice calls on lbm_batch_case(b, i).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <new>
 #include <string>
 #include <vector>
@@ -56,7 +57,7 @@ struct lbm_batch {
   int nwork = 0;
   int variant = 0;
   int nh = 1;
-  bool collapse = false;
+  int form = 0;  // 0 populations, 1 C state (collapse_h), 2 FP16 g and C (storage 1)
   bool work_valid = false;
   cudaGraphExec_t graph = nullptr;
   int graph_nwork = -1, graph_variant = -1;
@@ -125,7 +126,7 @@ static lbm_status persistent_steps(lbm_batch *b, long long nsteps) {
   auto one_launch = [&](int steps) {
     cudaError_t r = cudaMemsetAsync(b->d_sync, 0, sizeof(lbm::GridSync), b->stream);
     if (r == cudaSuccess)
-      r = lbm::launch_sweep_persistent(b->nh, b->collapse, b->d_cases, b->d_work, b->nwork, 0, steps, b->d_sync,
+      r = lbm::launch_sweep_persistent(b->nh, b->form, b->d_cases, b->d_work, b->nwork, 0, steps, b->d_sync,
                                        b->spin_limit, b->stream, b->variant, &grid);
     return r;
   };
@@ -134,7 +135,7 @@ static lbm_status persistent_steps(lbm_batch *b, long long nsteps) {
   if (full > 0 && (!b->pgraph || b->pgraph_nwork != b->nwork || b->pgraph_variant != b->variant ||
                    b->pgraph_limit != b->spin_limit)) {
     // kernel attributes and occupancy are queried outside the capture
-    e = lbm::launch_sweep_persistent(b->nh, b->collapse, b->d_cases, b->d_work, b->nwork, 0, 0, b->d_sync,
+    e = lbm::launch_sweep_persistent(b->nh, b->form, b->d_cases, b->d_work, b->nwork, 0, 0, b->d_sync,
                                      b->spin_limit, b->stream, b->variant, &grid);
     if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step persistent prepare");
     if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
@@ -207,7 +208,7 @@ size_t lbm_batch_required_bytes(const lbm_params *cases, int ncases) {
   size_t total = 0;
   for (int i = 0; i < ncases; ++i) {
     const size_t b = lbm_required_bytes(&cases[i]);
-    if (b == 0 || cases[i].storage != 0 || cases[i].open_x) return 0;  // periodic FP32 states only
+    if (b == 0 || cases[i].open_x) return 0;  // periodic x only
     total += align_up(b, kAlign);
   }
   total += batch_table_bytes(ncases) + batch_err_bytes(ncases) + batch_sync_bytes();
@@ -225,15 +226,15 @@ lbm_status lbm_batch_create(const lbm_params *cases, int ncases, void *dev_arena
   if (arena_bytes < need) return LBM_E_NOMEM;
   for (int i = 0; i < ncases; ++i) {
     if (cases[i].ncomp != cases[0].ncomp || cases[i].collapse_h != cases[0].collapse_h || cases[i].fd_scheme != 0 ||
-        cases[i].storage != 0)
-      return LBM_E_INVAL;  // one kernel: same component count and state form, central differences, FP32
+        cases[i].storage != cases[0].storage)
+      return LBM_E_INVAL;  // one kernel: same component count and state form, central differences
   }
   lbm_batch *b = new (std::nothrow) lbm_batch();
   if (!b) return LBM_E_NOMEM;
   b->n = ncases;
   b->stream = (cudaStream_t)cuda_stream;
   b->nh = cases[0].ncomp - 1;
-  b->collapse = cases[0].collapse_h != 0;
+  b->form = cases[0].storage == 1 ? 2 : (cases[0].collapse_h ? 1 : 0);
   b->active.assign(ncases, 1);
   char *base = (char *)dev_arena;
   size_t off = 0;
@@ -285,10 +286,10 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int reps, int *chosen) {
     e = b->build_work(v, &nw);
     if (e != cudaSuccess || nw == 0) break;
     // parity 0 reads every case's current state and writes its spare buffers
-    e = lbm::launch_batched_step(b->nh, b->collapse, b->d_cases, b->d_work, nw, 0, b->stream, v);
+    e = lbm::launch_batched_step(b->nh, b->form, b->d_cases, b->d_work, nw, 0, b->stream, v);
     if (e != cudaSuccess) break;
     cudaEventRecord(e0, b->stream);
-    for (int r = 0; r < reps; ++r) lbm::launch_batched_step(b->nh, b->collapse, b->d_cases, b->d_work, nw, 0, b->stream, v);
+    for (int r = 0; r < reps; ++r) lbm::launch_batched_step(b->nh, b->form, b->d_cases, b->d_work, nw, 0, b->stream, v);
     cudaEventRecord(e1, b->stream);
     e = cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -326,14 +327,14 @@ lbm_status lbm_batch_step(lbm_batch *b, long long nsteps) {
   const long long graphs = capturable ? nsteps / kGraphSteps : 0;
   if (graphs > 0 && (!b->graph || b->graph_nwork != b->nwork || b->graph_variant != b->variant)) {
     // kernel attributes are set outside the capture
-    e = lbm::launch_batched_step(b->nh, b->collapse, b->d_cases, b->d_work, 0, 0, b->stream, b->variant);
+    e = lbm::launch_batched_step(b->nh, b->form, b->d_cases, b->d_work, 0, 0, b->stream, b->variant);
     if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step prepare");
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     for (int t = 0; t < kGraphSteps && e == cudaSuccess; ++t)
-      e = lbm::launch_batched_step(b->nh, b->collapse, b->d_cases, b->d_work, b->nwork, t & 1, b->stream, b->variant);
+      e = lbm::launch_batched_step(b->nh, b->form, b->d_cases, b->d_work, b->nwork, t & 1, b->stream, b->variant);
     cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
     if (e == cudaSuccess) e = ec;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
@@ -344,7 +345,7 @@ lbm_status lbm_batch_step(lbm_batch *b, long long nsteps) {
   }
   for (long long r = 0; r < graphs && e == cudaSuccess; ++r) e = cudaGraphLaunch(b->graph, b->stream);
   for (long long t = graphs * kGraphSteps; t < nsteps && e == cudaSuccess; ++t)
-    e = lbm::launch_batched_step(b->nh, b->collapse, b->d_cases, b->d_work, b->nwork, (int)(t & 1), b->stream,
+    e = lbm::launch_batched_step(b->nh, b->form, b->d_cases, b->d_work, b->nwork, (int)(t & 1), b->stream,
                                  b->variant);
   if (e != cudaSuccess) return b->cuda_fail(e, "lbm_batch_step launch");
   std::vector<unsigned> err(b->n);
@@ -372,6 +373,82 @@ lbm_status lbm_batch_set_persistent(lbm_batch *b, int on, long long spin_limit) 
   b->spin_limit = spin_limit == 0 ? kDefaultSpinLimit : spin_limit;
   if (b->persistent && !lbm::batched_variant_is_sweep(b->nh, b->variant)) b->variant = 0;
   b->work_valid = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_run(lbm_batch *b, const lbm_run_opts *opts, lbm_obs *out, int *outcome, long long *steps) {
+  if (!b || !opts || !out || !outcome) return LBM_E_INVAL;
+  if (opts->window < 1 || !(opts->rtol > 0) || opts->max_steps < opts->window || !(opts->top_margin >= 0))
+    return b->fail(LBM_E_INVAL, "lbm_batch_run: need window >= 1, rtol > 0, max_steps >= window, top_margin >= 0");
+  const int n = b->n;
+  std::vector<std::vector<double>> ys(n);
+  std::vector<double> top(n, 0.0);
+  std::vector<long long> ran(n, 0);
+  std::vector<char> running(n, 0);
+  int left = 0;
+  for (int i = 0; i < n; ++i) {
+    outcome[i] = LBM_RUN_SKIPPED;
+    if (steps) steps[i] = 0;
+    if (!b->active[i] || !b->h[i]->initialized) continue;
+    lbm_obs o{};
+    lbm_status st = lbm_observables(b->h[i], &o);
+    if (st != LBM_OK) return b->fail(st, std::string("lbm_batch_run: ") + lbm_last_error(b->h[i]));
+    ys[i].push_back(o.centroid[1]);
+    top[i] = (double)(b->h[i]->prm.ny - 1) - opts->top_margin * o.d_eq;
+    running[i] = 1;
+    ++left;
+  }
+  // window-averaged rise velocities of case i so far
+  auto velocities = [&](int i) {
+    std::vector<double> u;
+    for (size_t k = 1; k < ys[i].size(); ++k) u.push_back((ys[i][k] - ys[i][k - 1]) / (double)opts->window);
+    return u;
+  };
+  auto finish = [&](int i, int result, const lbm_obs &o) {
+    const std::vector<double> u = velocities(i);
+    const double U = u.empty() ? 0.0 : u.back();
+    double raw[15];
+    for (int q = 0; q < 15; ++q) raw[q] = o.raw[q];
+    raw[10] = U * raw[6];
+    lbm_postprocess(&b->h[i]->prm, raw, &out[i]);
+    out[i].step = o.step;
+    out[i].y_integrated = o.y_integrated;
+    outcome[i] = result;
+    if (steps) steps[i] = ran[i];
+    running[i] = 0;
+    b->active[i] = 0;
+    b->work_valid = false;
+    --left;
+  };
+  while (left > 0) {
+    lbm_status st = lbm_batch_step(b, opts->window);
+    if (st != LBM_OK && st != LBM_E_DIVERGED) return st;
+    for (int i = 0; i < n; ++i) {
+      if (!running[i]) continue;
+      ran[i] += opts->window;
+      lbm_obs o{};
+      if (!b->active[i]) {  // deactivated by lbm_batch_step: non-finite values
+        lbm_observables(b->h[i], &o);
+        finish(i, LBM_RUN_DIVERGED, o);
+        continue;
+      }
+      st = lbm_observables(b->h[i], &o);
+      if (st != LBM_OK) return b->fail(st, std::string("lbm_batch_run: ") + lbm_last_error(b->h[i]));
+      if (!std::isfinite(o.centroid[1]) || !std::isfinite(o.rise_velocity)) {
+        finish(i, LBM_RUN_DIVERGED, o);
+        continue;
+      }
+      ys[i].push_back(o.centroid[1]);
+      const std::vector<double> u = velocities(i);
+      const size_t m = u.size();
+      bool steady = m >= 3;
+      for (size_t j = 1; steady && j <= 2; ++j)
+        steady = std::fabs(u[m - j] - u[m - j - 1]) < opts->rtol * std::fabs(u[m - j]);
+      if (steady) finish(i, LBM_RUN_TERMINAL, o);
+      else if (o.centroid[1] > top[i]) finish(i, LBM_RUN_TOP, o);
+      else if (ran[i] >= opts->max_steps) finish(i, LBM_RUN_MAX_STEPS, o);
+    }
+  }
   return LBM_OK;
 }
 

@@ -388,13 +388,17 @@ void batched_variant_tile(int nh, int v, int *tx, int *ty) {
   else VariantTable<2, 0>::tile(v, tx, ty);
 }
 
-cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+cudaError_t launch_batched_step(int nh, int form, const BatchCase *cases, const WorkItem *work, int nwork,
                                 int parity, cudaStream_t s, int v) {
   if (v < 0 || v >= batched_variant_count(nh)) v = 0;
   const int ns = sweep_batched_count(nh);
-  if (v < ns) return launch_sweep_batched(nh, collapse_h, cases, work, nwork, parity, s, v);
+  if (v < ns) return launch_sweep_batched(nh, form, cases, work, nwork, parity, s, v);
   v -= ns;
-  if (collapse_h) {
+  if (form == 2) {
+    if (nh == 1) return VariantTable<1, 2>::launch_batched(v, cases, work, nwork, parity, s);
+    return VariantTable<2, 2>::launch_batched(v, cases, work, nwork, parity, s);
+  }
+  if (form == 1) {
     if (nh == 1) return VariantTable<1, 1>::launch_batched(v, cases, work, nwork, parity, s);
     return VariantTable<2, 1>::launch_batched(v, cases, work, nwork, parity, s);
   }

@@ -68,16 +68,17 @@ bool batched_variant_is_sweep(int nh, int v);
 void batched_variant_tile(int nh, int v, int *tx, int *ty);
 int sweep_batched_count(int nh);
 void sweep_batched_shape(int nh, int v, int *tx, int *rows);
-cudaError_t launch_sweep_batched(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+// form: 0 populations g, h; 1 g and C (collapse_h); 2 FP16 g deviations and C
+cudaError_t launch_sweep_batched(int nh, int form, const BatchCase *cases, const WorkItem *work, int nwork,
                                  int parity, cudaStream_t s, int v);
-cudaError_t launch_batched_step(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+cudaError_t launch_batched_step(int nh, int form, const BatchCase *cases, const WorkItem *work, int nwork,
                                 int parity, cudaStream_t s, int v);
 // nsteps time steps of every work item in one persistent cooperative launch
 // (sweep configurations v < sweep_batched_count(nh) only): the CTAs that fit
 // on the device at once share the items of a step and meet at a grid barrier
 // between steps; a barrier wait gives up after spin_limit polls, sets
 // kSyncTimeout in sync->status and the kernel returns.  *grid = CTAs launched.
-cudaError_t launch_sweep_persistent(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+cudaError_t launch_sweep_persistent(int nh, int form, const BatchCase *cases, const WorkItem *work, int nwork,
                                     int parity0, int nsteps, GridSync *sync, long long spin_limit, cudaStream_t s,
                                     int v, int *grid);
 // Launch configurations of the fused step: row sweeps (strip width, rows per
@@ -85,7 +86,7 @@ cudaError_t launch_sweep_persistent(int nh, bool collapse_h, const BatchCase *ca
 int sweep_variant_count(const DevParams &P);
 const char *sweep_variant_name(const DevParams &P, int v);
 // Configuration a handle starts with: the sweep that measured fastest on the
-// 2048 x 4096 rising bubble (58 x 2 strips, 128 threads, 3 CTAs per SM).
+// 2048 x 4096 rising bubble (60 x 2 strips, 160 threads, 3 CTAs per SM).
 int sweep_default_variant(const DevParams &P);
 cudaError_t launch_sweep_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v);
 int fused_variant_count(const DevParams &P);

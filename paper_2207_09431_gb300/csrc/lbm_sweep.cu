@@ -233,6 +233,196 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
   };
   issue(j0);
 
+  // ---- stage 0: C and rho of row r0 (3-ring column c0), from the loads of
+  // the previous step
+  auto stage0 = [&]() {
+    float cst[NH];
+#pragma unroll
+    for (int q = 0; q < NH; ++q) {
+      if constexpr (FORM == 0) {
+        float acc = 0.f;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) acc += nh[q * 9 + a];
+        cst[q] = acc;
+      } else {
+        cst[q] = nh[q];
+      }
+    }
+    s.cr[s0][c0] = PV::make(cst, node_rho<NH>(P, cst));
+  };
+  // ---- stage 1: fields of row r1 (2-ring column c1): the arithmetic, then
+  // the stores of its results
+  auto stage1_compute = [&](const float (&gv)[9], NodeFields &f) {
+    const int cdn = ring_dn<S::D3>(s1c), cup = ring_up<S::D3>(s1c);
+    float cn[NH][9], rn[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const V v = s.cr[row_slot(ey(a), cdn, s1c, cup)][c1 + 1 + ex(a)];
+#pragma unroll
+      for (int q = 0; q < NH; ++q) cn[q][a] = PV::comp(v, q);
+      rn[a] = PV::last(v);
+    }
+    node_fields<NH>(P, gv, cn, rn, f);
+  };
+  auto stage1_store = [&](const float (&gv)[9], const NodeFields &f) {
+    s.mp[s1m][c1] = PV::make(f.mu, f.p);
+    if (c1 >= 1 && c1 <= TX + 2) {
+      float rec[4 * S::NQ];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) rec[a] = gv[a];
+      rec[9] = f.ux;
+      rec[10] = f.uy;
+      rec[11] = f.rx;
+      rec[12] = f.ry;
+#pragma unroll
+      for (int q = 0; q < NH; ++q) {
+        rec[13 + q] = f.mu[q] - f.mu[2];
+        rec[13 + NH + q] = f.gCx[q];
+        rec[13 + 2 * NH + q] = f.gCy[q];
+      }
+      if constexpr (REC) {
+#pragma unroll
+        for (int q = 0; q < NH; ++q) rec[13 + 3 * NH + q] = f.C[q];
+        rec[13 + 4 * NH] = f.rho;
+        rec[14 + 4 * NH] = f.irho;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          rec[15 + 4 * NH + k] = f.Dr[k];
+#pragma unroll
+          for (int q = 0; q < NH; ++q) rec[19 + 4 * NH + 4 * q + k] = f.DC[q][k];
+        }
+      }
+#pragma unroll
+      for (int k = S::NR; k < 4 * S::NQ; ++k) rec[k] = 0.f;
+#pragma unroll
+      for (int k = 0; k < S::NQ; ++k)
+        s.da[k][s1a][c1 - 1] = make_float4(rec[4 * k], rec[4 * k + 1], rec[4 * k + 2], rec[4 * k + 3]);
+    }
+  };
+  auto stage1_values = [&](float (&gv)[9]) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      if constexpr (FORM == 2) gv[a] = g16_decode(nP, ngh[a], a, P.g16_inv_scale);
+      else gv[a] = ng[a];
+    }
+  };
+  // ---- stage 3: arriving populations of output row r3
+  auto stage3 = [&](int j, int r3) {
+    const int sdn = ring_dn<S::DB>(s3), sup = ring_up<S::DB>(s3);
+    float gy[9], hy[NH][9], svy[NH];
+#pragma unroll
+    for (int q = 0; q < NH; ++q) svy[q] = s.svb[q][s3][c3 + 1];
+    const float2 uv = s.uvb[s3][c3 + 1];
+    if (per || (j >= 1 && j + RS <= ny - 1)) {
+      // no output row of this step is next to a wall
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        const int ss = row_slot(-ey(a), sdn, s3, sup), cs = c3 + 1 - ex(a);  // source row r3 - e_a
+        s.post.get(a, ss, cs, a, gy, hy);
+      }
+    } else {
+      const bool lo = r3 == 0, hi = r3 == ny - 1;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        // half-way bounce-back: a source row beyond the wall means the
+        // population left r3 in -e_a
+        const bool bb = (ey(a) > 0 && lo) || (ey(a) < 0 && hi);
+        const int ss = bb ? s3 : row_slot(-ey(a), sdn, s3, sup);
+        const int cs = bb ? c3 + 1 : c3 + 1 - ex(a);
+        const int b = bb ? opp(a) : a;
+        s.post.get(b, ss, cs, a, gy, hy);
+      }
+    }
+    store_node<NH, FORM>(P, B, plane, (long long)r3 * pitch + x3, gy, hy, svy, uv.x, uv.y);
+  };
+  // ---- stage 2: collision of row r2 (1-ring column c2): the arithmetic,
+  // then the stores of its results
+  struct Collided {
+    NodeCenter nc;
+    float g2[9], hs[NH][9], sv[NH], tn, gd2;
+  };
+  auto stage2_compute = [&](int r2, float tprev, Collided &o) {
+    const int cdn = ring_dn<S::D3>(s2c), cup = ring_up<S::D3>(s2c);
+    int mdn = ring_dn<S::D2>(s2m), mup = ring_up<S::D2>(s2m);
+    if (!per) {
+      // mu and p one row beyond a wall: the mirror row is row r2 itself
+      if (r2 == 0) mdn = s2m;
+      if (r2 == ny - 1) mup = s2m;
+    }
+    float pn[9], mun[NH][9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const V mp = s.mp[row_slot(ey(a), mdn, s2m, mup)][c2 + 1 + ex(a)];
+      pn[a] = PV::last(mp);
+#pragma unroll
+      for (int q = 0; q < NH; ++q) mun[q][a] = PV::comp(mp, q);
+    }
+    float rec[4 * S::NQ];
+#pragma unroll
+    for (int k = 0; k < S::NQ; ++k) {
+      const float4 w = s.da[k][s2a][c2];
+      rec[4 * k] = w.x;
+      rec[4 * k + 1] = w.y;
+      rec[4 * k + 2] = w.z;
+      rec[4 * k + 3] = w.w;
+    }
+#pragma unroll
+    for (int a = 0; a < 9; ++a) o.g2[a] = rec[a];
+    NodeCenter &nc = o.nc;
+    nc.ux = rec[9];
+    nc.uy = rec[10];
+    nc.grx = rec[11];
+    nc.gry = rec[12];
+    nc.p = pn[0];
+#pragma unroll
+    for (int q = 0; q < NH; ++q) {
+      nc.dmu[q] = rec[13 + q];
+      nc.gCx[q] = rec[13 + NH + q];
+      nc.gCy[q] = rec[13 + 2 * NH + q];
+    }
+    if constexpr (REC) {
+#pragma unroll
+      for (int q = 0; q < NH; ++q) nc.C[q] = rec[13 + 3 * NH + q];
+      nc.rho = rec[13 + 4 * NH];
+      nc.irho = rec[14 + 4 * NH];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        nc.Dr[k] = rec[15 + 4 * NH + k];
+#pragma unroll
+        for (int q = 0; q < NH; ++q) nc.DC[q][k] = rec[19 + 4 * NH + 4 * q + k];
+      }
+    } else {
+      // C and rho of the 3x3 stencil from the ring
+      float rn[9], cn[NH][9];
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        const V cr = s.cr[row_slot(ey(a), cdn, s2c, cup)][c2 + 2 + ex(a)];
+        rn[a] = PV::last(cr);
+#pragma unroll
+        for (int q = 0; q < NH; ++q) cn[q][a] = PV::comp(cr, q);
+      }
+      nc.rho = rn[0];
+      nc.irho = __fdividef(1.0f, rn[0]);
+      pair_diff(rn, nc.Dr);
+#pragma unroll
+      for (int q = 0; q < NH; ++q) {
+        nc.C[q] = cn[q][0];
+        pair_diff(cn[q], nc.DC[q]);
+      }
+    }
+    node_collide<NH>(P, nc, pn, mun, o.g2, tprev, o.hs, o.sv, o.tn, o.gd2);
+  };
+  auto stage2_store = [&](int r2, long long k2, const Collided &o) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      s.post.put(a, s2b, c2, o.g2[a], o.hs);
+    }
+#pragma unroll
+    for (int q = 0; q < NH; ++q) s.svb[q][s2b][c2] = o.sv[q];
+    s.uvb[s2b][c2] = make_float2(o.nc.ux, o.nc.uy);
+    if (own2 && r2 >= ys && r2 < ye) store_diagnostics<NH>(B, plane, k2, o.tn, o.gd2, o.sv, o.nc);
+  };
+
   for (int j = j0; j < ye; j += RS) {
     int r0, r1, r2;
     bool a0, a1, a2;
@@ -241,190 +431,21 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
     const bool a3 = out3 && r3 >= ys && r3 < ye;
     const long long k2 = (long long)(per && !interior(j) ? wrap_periodic(r2, ny) : r2) * pitch + x2c;
 
-    // ---- stage 0: C and rho of row r0 (3-ring column c0), from the loads of
-    // the previous step
-    if (a0) {
-      float cst[NH];
-#pragma unroll
-      for (int q = 0; q < NH; ++q) {
-        if constexpr (FORM == 0) {
-          float acc = 0.f;
-#pragma unroll
-          for (int a = 0; a < 9; ++a) acc += nh[q * 9 + a];
-          cst[q] = acc;
-        } else {
-          cst[q] = nh[q];
-        }
-      }
-      s.cr[s0][c0] = PV::make(cst, node_rho<NH>(P, cst));
-    }
-
-    // ---- stage 1: fields of row r1 (2-ring column c1)
+    if (a0) stage0();
     if (a1) {
       float gv[9];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        if constexpr (FORM == 2) gv[a] = g16_decode(nP, ngh[a], a, P.g16_inv_scale);
-        else gv[a] = ng[a];
-      }
-      const int cdn = ring_dn<S::D3>(s1c), cup = ring_up<S::D3>(s1c);
-      float cn[NH][9], rn[9];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        const V v = s.cr[row_slot(ey(a), cdn, s1c, cup)][c1 + 1 + ex(a)];
-#pragma unroll
-        for (int q = 0; q < NH; ++q) cn[q][a] = PV::comp(v, q);
-        rn[a] = PV::last(v);
-      }
+      stage1_values(gv);
       NodeFields f;
-      node_fields<NH>(P, gv, cn, rn, f);
-      s.mp[s1m][c1] = PV::make(f.mu, f.p);
-      if (c1 >= 1 && c1 <= TX + 2) {
-        float rec[4 * S::NQ];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) rec[a] = gv[a];
-        rec[9] = f.ux;
-        rec[10] = f.uy;
-        rec[11] = f.rx;
-        rec[12] = f.ry;
-#pragma unroll
-        for (int q = 0; q < NH; ++q) {
-          rec[13 + q] = f.mu[q] - f.mu[2];
-          rec[13 + NH + q] = f.gCx[q];
-          rec[13 + 2 * NH + q] = f.gCy[q];
-        }
-        if constexpr (REC) {
-#pragma unroll
-          for (int q = 0; q < NH; ++q) rec[13 + 3 * NH + q] = f.C[q];
-          rec[13 + 4 * NH] = f.rho;
-          rec[14 + 4 * NH] = f.irho;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            rec[15 + 4 * NH + k] = f.Dr[k];
-#pragma unroll
-            for (int q = 0; q < NH; ++q) rec[19 + 4 * NH + 4 * q + k] = f.DC[q][k];
-          }
-        }
-#pragma unroll
-        for (int k = S::NR; k < 4 * S::NQ; ++k) rec[k] = 0.f;
-#pragma unroll
-        for (int k = 0; k < S::NQ; ++k)
-          s.da[k][s1a][c1 - 1] = make_float4(rec[4 * k], rec[4 * k + 1], rec[4 * k + 2], rec[4 * k + 3]);
-      }
+      stage1_compute(gv, f);
+      stage1_store(gv, f);
     }
     const float tprev = nt;
     issue(j + RS);  // the next step's loads
-
-    // ---- stage 3: arriving populations of output row r3
-    if (a3) {
-      const int sdn = ring_dn<S::DB>(s3), sup = ring_up<S::DB>(s3);
-      float gy[9], hy[NH][9], svy[NH];
-#pragma unroll
-      for (int q = 0; q < NH; ++q) svy[q] = s.svb[q][s3][c3 + 1];
-      const float2 uv = s.uvb[s3][c3 + 1];
-      if (per || (j >= 1 && j + RS <= ny - 1)) {
-        // no output row of this step is next to a wall
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-          const int ss = row_slot(-ey(a), sdn, s3, sup), cs = c3 + 1 - ex(a);  // source row r3 - e_a
-          s.post.get(a, ss, cs, a, gy, hy);
-        }
-      } else {
-        const bool lo = r3 == 0, hi = r3 == ny - 1;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-          // half-way bounce-back: a source row beyond the wall means the
-          // population left r3 in -e_a
-          const bool bb = (ey(a) > 0 && lo) || (ey(a) < 0 && hi);
-          const int ss = bb ? s3 : row_slot(-ey(a), sdn, s3, sup);
-          const int cs = bb ? c3 + 1 : c3 + 1 - ex(a);
-          const int b = bb ? opp(a) : a;
-          s.post.get(b, ss, cs, a, gy, hy);
-        }
-      }
-      store_node<NH, FORM>(P, B, plane, (long long)r3 * pitch + x3, gy, hy, svy, uv.x, uv.y);
-    }
-
-    // ---- stage 2: collision of row r2 (1-ring column c2)
+    if (a3) stage3(j, r3);
     if (a2) {
-      const int cdn = ring_dn<S::D3>(s2c), cup = ring_up<S::D3>(s2c);
-      int mdn = ring_dn<S::D2>(s2m), mup = ring_up<S::D2>(s2m);
-      if (!per) {
-        // mu and p one row beyond a wall: the mirror row is row r2 itself
-        if (r2 == 0) mdn = s2m;
-        if (r2 == ny - 1) mup = s2m;
-      }
-      float pn[9], mun[NH][9], g2[9];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        const V mp = s.mp[row_slot(ey(a), mdn, s2m, mup)][c2 + 1 + ex(a)];
-        pn[a] = PV::last(mp);
-#pragma unroll
-        for (int q = 0; q < NH; ++q) mun[q][a] = PV::comp(mp, q);
-      }
-      float rec[4 * S::NQ];
-#pragma unroll
-      for (int k = 0; k < S::NQ; ++k) {
-        const float4 w = s.da[k][s2a][c2];
-        rec[4 * k] = w.x;
-        rec[4 * k + 1] = w.y;
-        rec[4 * k + 2] = w.z;
-        rec[4 * k + 3] = w.w;
-      }
-#pragma unroll
-      for (int a = 0; a < 9; ++a) g2[a] = rec[a];
-      NodeCenter nc;
-      nc.ux = rec[9];
-      nc.uy = rec[10];
-      nc.grx = rec[11];
-      nc.gry = rec[12];
-      nc.p = pn[0];
-#pragma unroll
-      for (int q = 0; q < NH; ++q) {
-        nc.dmu[q] = rec[13 + q];
-        nc.gCx[q] = rec[13 + NH + q];
-        nc.gCy[q] = rec[13 + 2 * NH + q];
-      }
-      if constexpr (REC) {
-#pragma unroll
-        for (int q = 0; q < NH; ++q) nc.C[q] = rec[13 + 3 * NH + q];
-        nc.rho = rec[13 + 4 * NH];
-        nc.irho = rec[14 + 4 * NH];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          nc.Dr[k] = rec[15 + 4 * NH + k];
-#pragma unroll
-          for (int q = 0; q < NH; ++q) nc.DC[q][k] = rec[19 + 4 * NH + 4 * q + k];
-        }
-      } else {
-        // C and rho of the 3x3 stencil from the ring
-        float rn[9], cn[NH][9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-          const V cr = s.cr[row_slot(ey(a), cdn, s2c, cup)][c2 + 2 + ex(a)];
-          rn[a] = PV::last(cr);
-#pragma unroll
-          for (int q = 0; q < NH; ++q) cn[q][a] = PV::comp(cr, q);
-        }
-        nc.rho = rn[0];
-        nc.irho = __fdividef(1.0f, rn[0]);
-        pair_diff(rn, nc.Dr);
-#pragma unroll
-        for (int q = 0; q < NH; ++q) {
-          nc.C[q] = cn[q][0];
-          pair_diff(cn[q], nc.DC[q]);
-        }
-      }
-      float hs[NH][9], sv[NH], tn, gd2;
-      node_collide<NH>(P, nc, pn, mun, g2, tprev, hs, sv, tn, gd2);
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        s.post.put(a, s2b, c2, g2[a], hs);
-      }
-#pragma unroll
-      for (int q = 0; q < NH; ++q) s.svb[q][s2b][c2] = sv[q];
-      s.uvb[s2b][c2] = make_float2(nc.ux, nc.uy);
-      if (own2 && r2 >= ys && r2 < ye) store_diagnostics<NH>(B, plane, k2, tn, gd2, sv, nc);
+      Collided o;
+      stage2_compute(r2, tprev, o);
+      stage2_store(r2, k2, o);
     }
 
     s0 = ring_add<S::D3, RS>(s0);
@@ -440,6 +461,12 @@ __device__ __forceinline__ void sweep_body(const DevParams &P, const FusedBuffer
   }
 }
 
+// Rows of a pipeline fill: the steps before a segment's first output row, as
+// rows of work (stage 0 starts 3 RS + RS ceil(6 / RS) rows before it).
+template <int RS>
+__host__ __device__ constexpr int fill_rows() { return 3 * RS + RS * ((6 + RS - 1) / RS); }
+
+// CTA (x, y) sweeps strip x over rows [y seg_len, (y + 1) seg_len).
 template <int TX, int RS, int NH, int FORM, int PER, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_step_sweep(DevParams P, FusedBuffers B, int seg_len) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -539,23 +566,24 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep_persistent(const BatchCase *
   }
 }
 
-// Segment length for a strip count: balances the waves of CTAs against the
-// per-segment overhead (3 + 2 + 1 extra rows of stages 0-2 at each end and
-// the steps that fill the pipeline).
-int choose_segment(int ny, int strips, int resident, int rs) {
+// Segment length for a strip count: the number of segments per strip that
+// minimises the rows the slowest CTA sweeps, waves x (segment rows + the
+// pipeline fill of fill rows), with the rows of a strip split evenly (a multiple of
+// rs each, the last segment the shortest).
+int choose_segment(int ny, int strips, int resident, int rs, int fill) {
   int best_len = ny;
-  double best_eff = -1.0;
-  for (int len = rs; len <= 1024; len += rs) {
-    const int nseg = (ny + len - 1) / len;
+  long long best_cost = -1;
+  for (int nseg = 1; nseg <= (ny + rs - 1) / rs; ++nseg) {
+    int len = (ny + nseg - 1) / nseg;
+    len = (len + rs - 1) / rs * rs;
+    if ((ny + len - 1) / len != nseg) continue;  // rounding merged two segments
     const long long total = (long long)strips * nseg;
     const long long waves = (total + resident - 1) / resident;
-    const double fill = (double)total / (double)(waves * resident);
-    const double eff = fill * (double)len / (double)(len + 6 + rs);
-    if (eff > best_eff + 1e-9) {
-      best_eff = eff;
+    const long long cost = waves * (len + fill);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
       best_len = len;
     }
-    if (len >= ny) break;
   }
   return best_len;
 }
@@ -580,7 +608,7 @@ cudaError_t launch_sweep_per(const DevParams &P, const FusedBuffers &B, cudaStre
     configured = true;
   }
   const int strips = (P.nx + TX - 1) / TX;
-  const int len = choose_segment(P.ny, strips, resident_per_sm * sms, RS);
+  const int len = choose_segment(P.ny, strips, resident_per_sm * sms, RS, fill_rows<RS>());
   const dim3 grd(strips, (P.ny + len - 1) / len);
   k_step_sweep<TX, RS, NH, FORM, PER, NT, MINB><<<grd, NT, smem, st>>>(P, B, len);
   return cudaGetLastError();
@@ -600,7 +628,7 @@ cudaError_t launch_sweep_t(const DevParams &P, const FusedBuffers &B, cudaStream
 // step / threads / minimum resident CTAs per SM.
 int sweep_variant_count(const DevParams &P) { return P.nh == 1 ? 13 : 4; }
 
-int sweep_default_variant(const DevParams &P) { return P.nh == 1 ? 11 : 0; }
+int sweep_default_variant(const DevParams &P) { return P.nh == 1 ? 9 : 0; }
 
 const char *sweep_variant_name(const DevParams &P, int v) {
   static const char *n1[13] = {"64x2/160/3", "32x4/160/3", "128x1/160/2", "64x4/288/2", "64x1/96/5",
@@ -738,24 +766,31 @@ static cudaError_t sweep_batched_dispatch(int v, const BatchCase *c, const WorkI
   }
 }
 
-cudaError_t launch_sweep_batched(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+cudaError_t launch_sweep_batched(int nh, int form, const BatchCase *cases, const WorkItem *work, int nwork,
                                  int parity, cudaStream_t s, int v) {
   if (v < 0 || v >= sweep_batched_count(nh)) v = 0;
-  if (nh == 1) return collapse_h ? sweep_batched_dispatch<1, 1>(v, cases, work, nwork, parity, s)
-                                 : sweep_batched_dispatch<1, 0>(v, cases, work, nwork, parity, s);
-  return collapse_h ? sweep_batched_dispatch<2, 1>(v, cases, work, nwork, parity, s)
-                    : sweep_batched_dispatch<2, 0>(v, cases, work, nwork, parity, s);
+  if (nh == 1) {
+    if (form == 2) return sweep_batched_dispatch<1, 2>(v, cases, work, nwork, parity, s);
+    if (form == 1) return sweep_batched_dispatch<1, 1>(v, cases, work, nwork, parity, s);
+    return sweep_batched_dispatch<1, 0>(v, cases, work, nwork, parity, s);
+  }
+  if (form == 2) return sweep_batched_dispatch<2, 2>(v, cases, work, nwork, parity, s);
+  if (form == 1) return sweep_batched_dispatch<2, 1>(v, cases, work, nwork, parity, s);
+  return sweep_batched_dispatch<2, 0>(v, cases, work, nwork, parity, s);
 }
 
-cudaError_t launch_sweep_persistent(int nh, bool collapse_h, const BatchCase *cases, const WorkItem *work, int nwork,
+cudaError_t launch_sweep_persistent(int nh, int form, const BatchCase *cases, const WorkItem *work, int nwork,
                                     int parity0, int nsteps, GridSync *sync, long long spin_limit, cudaStream_t s,
                                     int v, int *grid) {
   if (v < 0 || v >= sweep_batched_count(nh)) return cudaErrorInvalidValue;
-  if (nh == 1)
-    return collapse_h ? sweep_persistent_dispatch<1, 1>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid)
-                      : sweep_persistent_dispatch<1, 0>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid);
-  return collapse_h ? sweep_persistent_dispatch<2, 1>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid)
-                    : sweep_persistent_dispatch<2, 0>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid);
+  if (nh == 1) {
+    if (form == 2) return sweep_persistent_dispatch<1, 2>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid);
+    if (form == 1) return sweep_persistent_dispatch<1, 1>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid);
+    return sweep_persistent_dispatch<1, 0>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid);
+  }
+  if (form == 2) return sweep_persistent_dispatch<2, 2>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid);
+  if (form == 1) return sweep_persistent_dispatch<2, 1>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid);
+  return sweep_persistent_dispatch<2, 0>(v, cases, work, nwork, parity0, nsteps, sync, spin_limit, s, grid);
 }
 
 cudaError_t launch_sweep_step(const DevParams &P, const FusedBuffers &B, cudaStream_t s, int v) {

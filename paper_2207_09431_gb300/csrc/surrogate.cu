@@ -484,4 +484,66 @@ lbm_status surr_predict(surr_net *n, const double *X, int rows, double *y_mean, 
   return LBM_OK;
 }
 
+// Terminal states from the network where it is trusted, from the lattice
+// Boltzmann solver elsewhere (one batch of the untrusted cases in the caller's
+// arena, run by lbm_batch_run).
+lbm_status surr_answer(surr_net *n, const double *X, const lbm_params *cases, const lbm_bubble *bubbles, int rows,
+                       double max_spread, double noise_amp, const lbm_run_opts *opts, void *dev_arena,
+                       size_t arena_bytes, double *y_out, int *used_fallback, int *fallback_outcome) {
+  if (!n || !X || !cases || !bubbles || !opts || !y_out || !used_fallback || rows < 1 || !(max_spread > 0))
+    return LBM_E_INVAL;
+  std::vector<double> mean((size_t)rows * 2), spread((size_t)rows * 2);
+  std::vector<int> outside(rows);
+  lbm_status st = surr_predict(n, X, rows, mean.data(), spread.data(), outside.data());
+  if (st != LBM_OK) return st;
+  std::vector<int> fb;
+  for (int r = 0; r < rows; ++r) {
+    const bool trusted = !outside[r] && spread[2 * r] < max_spread && spread[2 * r + 1] < max_spread;
+    used_fallback[r] = trusted ? 0 : 1;
+    if (fallback_outcome) fallback_outcome[r] = LBM_RUN_SKIPPED;
+    // the network is trained on (log U_t, log C_D)
+    y_out[2 * r] = trusted ? std::exp(mean[2 * r]) : NAN;
+    y_out[2 * r + 1] = trusted ? std::exp(mean[2 * r + 1]) : NAN;
+    if (!trusted) fb.push_back(r);
+  }
+  if (fb.empty()) return LBM_OK;
+  std::vector<lbm_params> sub;
+  for (int r : fb) sub.push_back(cases[r]);
+  const size_t need = lbm_batch_required_bytes(sub.data(), (int)sub.size());
+  if (need == 0) {
+    n->last_error = "surr_answer: a fallback case's parameters are not valid for a batch";
+    return LBM_E_INVAL;
+  }
+  if (!dev_arena || arena_bytes < need) {
+    n->last_error = "surr_answer: the arena is smaller than lbm_batch_required_bytes of the fallback cases";
+    return LBM_E_NOMEM;
+  }
+  lbm_batch *b = nullptr;
+  st = lbm_batch_create(sub.data(), (int)sub.size(), dev_arena, arena_bytes, n->stream, &b);
+  if (st != LBM_OK) {
+    n->last_error = "surr_answer: lbm_batch_create failed";
+    return st;
+  }
+  for (size_t k = 0; k < fb.size() && st == LBM_OK; ++k)
+    st = lbm_init_bubbles(lbm_batch_case(b, (int)k), &bubbles[fb[k]], 1, (unsigned long long)fb[k], noise_amp);
+  if (st == LBM_OK) st = lbm_batch_autotune(b, 2, nullptr);
+  std::vector<lbm_obs> obs(fb.size());
+  std::vector<int> outc(fb.size());
+  if (st == LBM_OK) st = lbm_batch_run(b, opts, obs.data(), outc.data(), nullptr);
+  if (st != LBM_OK) {
+    n->last_error = std::string("surr_answer: ") + lbm_batch_last_error(b);
+    lbm_batch_destroy(b);
+    return st;
+  }
+  for (size_t k = 0; k < fb.size(); ++k) {
+    const int r = fb[k];
+    const bool ok = outc[k] != LBM_RUN_DIVERGED;
+    y_out[2 * r] = ok ? obs[k].rise_velocity : NAN;
+    y_out[2 * r + 1] = ok ? obs[k].drag_coefficient : NAN;
+    if (fallback_outcome) fallback_outcome[r] = outc[k];
+  }
+  lbm_batch_destroy(b);
+  return LBM_OK;
+}
+
 }  // extern "C"

@@ -49,6 +49,14 @@ class lbm_bubble(ctypes.Structure):
     _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("r", ctypes.c_double), ("comp", ctypes.c_int)]
 
 
+class lbm_run_opts(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_longlong), ("rtol", ctypes.c_double), ("max_steps", ctypes.c_longlong),
+                ("top_margin", ctypes.c_double)]
+
+
+RUN_OUTCOMES = {0: "max_steps", 1: "terminal", 2: "top", -1: "diverged", -2: "skipped"}
+
+
 class lbm_obs(ctypes.Structure):
     _fields_ = [
         ("step", ctypes.c_longlong), ("mass", ctypes.c_double * 3), ("mass_thr", ctypes.c_double * 3),
@@ -70,8 +78,8 @@ EXPORTED = ["lbm_version", "lbm_required_bytes", "lbm_create", "lbm_init_bubbles
             "lbm_profile_step", "lbm_observables_static", "lbm_autotune", "lbm_kernel_config_count",
             "lbm_set_kernel_config", "lbm_batch_required_bytes", "lbm_batch_create", "lbm_batch_case",
             "lbm_batch_set_active", "lbm_batch_step", "lbm_batch_autotune", "lbm_batch_destroy",
-            "lbm_batch_last_error", "lbm_batch_set_persistent", "surr_param_count", "surr_required_bytes", "surr_create", "surr_destroy",
-            "surr_last_error", "surr_get_weights", "surr_forward_backward", "surr_train", "surr_predict"]
+            "lbm_batch_last_error", "lbm_batch_set_persistent", "lbm_batch_run", "surr_param_count", "surr_required_bytes", "surr_create", "surr_destroy",
+            "surr_last_error", "surr_get_weights", "surr_forward_backward", "surr_train", "surr_predict", "surr_answer"]
 
 
 def load_library(path: str | None = None):
@@ -117,6 +125,7 @@ def load_library(path: str | None = None):
     lib.lbm_batch_step.argtypes = [vp, ctypes.c_longlong]
     lib.lbm_batch_autotune.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
     lib.lbm_batch_set_persistent.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
+    lib.lbm_batch_run.argtypes = [vp, P(lbm_run_opts), P(lbm_obs), P(ctypes.c_int), P(ctypes.c_longlong)]
     lib.lbm_batch_destroy.argtypes = [vp]
     lib.lbm_batch_destroy.restype = None
     lib.lbm_batch_last_error.argtypes = [vp]
@@ -134,6 +143,9 @@ def load_library(path: str | None = None):
     lib.surr_train.argtypes = [vp, d, d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                ctypes.c_ulonglong, d]
     lib.surr_predict.argtypes = [vp, d, ctypes.c_int, d, d, P(ctypes.c_int)]
+    lib.surr_answer.argtypes = [vp, d, P(lbm_params), P(lbm_bubble), ctypes.c_int, ctypes.c_double,
+                                ctypes.c_double, P(lbm_run_opts), vp, ctypes.c_size_t, d, P(ctypes.c_int),
+                                P(ctypes.c_int)]
     lib.lbm_observables_static.argtypes = [P(lbm_params), vp, vp, ctypes.c_int, ctypes.c_longlong, d, vp]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
@@ -352,6 +364,24 @@ def lbm_batch_set_persistent(b, on: bool = True, spin_limit: int = 0):
                  "lbm_batch_set_persistent")
 
 
+def lbm_batch_run(b, ncases: int, window=2000, rtol=0.01, max_steps=40000, top_margin=1.5) -> list:
+    """Runs the batch's active cases to their terminal state; per case a dict
+    of the observables at the stop (rise_velocity = window-averaged U_t) with
+    'outcome' and 'steps_run'."""
+    opts = lbm_run_opts(int(window), float(rtol), int(max_steps), float(top_margin))
+    obs = (lbm_obs * ncases)()
+    outcome = (ctypes.c_int * ncases)()
+    steps = (ctypes.c_longlong * ncases)()
+    _check_batch(b, load_library().lbm_batch_run(b, ctypes.byref(opts), obs, outcome, steps), "lbm_batch_run")
+    res = []
+    for i in range(ncases):
+        d = obs_to_dict(obs[i])
+        d["outcome"] = RUN_OUTCOMES[outcome[i]]
+        d["steps_run"] = int(steps[i])
+        res.append(d)
+    return res
+
+
 def lbm_batch_destroy(b):
     if b:
         load_library().lbm_batch_destroy(b)
@@ -405,6 +435,10 @@ class Batch:
 
     def autotune(self, reps=3) -> int:
         return lbm_batch_autotune(self.b, reps)
+
+    def run(self, window=2000, rtol=0.01, max_steps=40000, top_margin=1.5) -> list:
+        """Every active case to its terminal state (see lbm_batch_run)."""
+        return lbm_batch_run(self.b, len(self.params), window, rtol, max_steps, top_margin)
 
     def set_persistent(self, on=True, spin_limit=0):
         """One cooperative launch for many steps (see lbm_batch_set_persistent)."""
@@ -502,6 +536,24 @@ def surr_predict(n, X):
     return mean, spread, np.array(list(outside), dtype=bool)
 
 
+def surr_answer(n, X, cases, bubbles, max_spread, noise_amp, window, rtol, max_steps, top_margin, arena_ptr,
+                arena_bytes):
+    """(y (rows x 2: U_t, C_D), used_fallback, fallback outcome per row) from
+    the network where trusted and the solver elsewhere (see include/lbm.h)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    rows = X.shape[0]
+    prs = (lbm_params * rows)(*[make_params(c) for c in cases])
+    bs = (lbm_bubble * rows)(*[lbm_bubble(float(b[0]), float(b[1]), float(b[2]), int(b[3])) for b in bubbles])
+    opts = lbm_run_opts(int(window), float(rtol), int(max_steps), float(top_margin))
+    y = np.zeros((rows, 2))
+    used = (ctypes.c_int * rows)()
+    outc = (ctypes.c_int * rows)()
+    _check_surr(n, load_library().surr_answer(n, _dptr(X), prs, bs, rows, float(max_spread), float(noise_amp),
+                                              ctypes.byref(opts), ctypes.c_void_p(arena_ptr), int(arena_bytes),
+                                              _dptr(y), used, outc), "surr_answer")
+    return y, np.array(used[:], dtype=bool), [RUN_OUTCOMES[o] for o in outc]
+
+
 class Surrogate:
     """Ensemble network with its torch-allocated arena and stream."""
 
@@ -535,6 +587,22 @@ class Surrogate:
 
     def predict(self, X):
         return surr_predict(self.n, X)
+
+    def answer(self, X, cases, bubbles, max_spread=0.05, noise_amp=1e-8, window=2000, rtol=0.05, max_steps=40000,
+               top_margin=1.5):
+        """Network where trusted, solver elsewhere (surr_answer); the solver's
+        batch arena is allocated here for every case, the most it can need."""
+        import torch
+
+        full = []
+        for c in cases:
+            q = dict(DEFAULTS)
+            q.update(c)
+            full.append(q)
+        nbytes = lbm_batch_required_bytes([make_params(c) for c in full])
+        arena = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.arena.device)
+        return surr_answer(self.n, X, full, bubbles, max_spread, noise_amp, window, rtol, max_steps, top_margin,
+                           arena.data_ptr(), nbytes)
 
 
 class Lattice:

@@ -34,54 +34,27 @@ def features(params: dict, meta: dict) -> np.ndarray:
                      math.log10(params["pl_k"] / eta_g)])
 
 
-def run_to_terminal(cases, window=2000, rtol=0.05, max_steps=40000, stream=None, device="cuda"):
+def run_to_terminal(cases, window=2000, rtol=0.05, max_steps=40000, stream=None, device="cuda", persistent=False):
     """Advances cases [(params, discs, meta), ...] together until each reaches
-    its terminal state.  The rise velocity is measured as the centroid
-    displacement (Eq. 44) per window, i.e. the window average of Eq. 43, because
-    the instantaneous value oscillates with the bubble shape.  Returns per-case
-    dicts with U_t, C_D (Eq. 37, through lbm_postprocess), steps, converged and
-    finite, and the wall time."""
+    its terminal state (lbm_batch_run: the rise velocity measured as the
+    centroid displacement per window, Eq. 44, because the instantaneous value
+    oscillates with the bubble shape).  Returns per-case dicts with U_t, C_D
+    (Eq. 37 at U_t), steps, converged and finite, and the wall time."""
     batch = lbm.Batch([c[0] for c in cases], device=device, stream=stream)
+    if persistent:
+        batch.set_persistent(True)
     for i, (p, b, _) in enumerate(cases):
         batch.case(i).set_fields(inputs.bubble_fields(p["nx"], p["ny"], 2, p["xi"], b, seed=i, noise=1e-8))
     batch.autotune(reps=2)
-    n = len(cases)
-    done = [False] * n
-    out = [dict(U_t=math.nan, C_D=math.nan, steps=0, converged=False, finite=True) for _ in range(n)]
-    ys = [[batch.case(i).observables()["centroid"][1]] for i in range(n)]
     t0 = time.perf_counter()
-    steps = 0
-    while steps < max_steps and not all(done):
-        try:
-            batch.step(window)
-        except lbm.LbmError as err:
-            if err.status != -4:
-                raise
-        steps += window
-        for i in range(n):
-            if done[i]:
-                continue
-            ob = batch.case(i).observables()
-            y = ob["centroid"][1]
-            if not (np.isfinite(y) and np.isfinite(ob["rise_velocity"])):
-                out[i].update(finite=False, steps=steps)
-                done[i] = True
-                batch.set_active(i, False)
-                continue
-            ys[i].append(y)
-            u = np.diff(ys[i]) / window
-            p = cases[i][0]
-            top = p["ny"] - 1.5 * 2.0 * cases[i][1][0][2]
-            steady = len(u) >= 3 and all(abs(u[-j] - u[-j - 1]) < rtol * abs(u[-j]) for j in (1, 2))
-            if steady or y > top or steps >= max_steps:
-                raw = np.array(ob["raw"])
-                raw[10] = u[-1] * raw[6]           # window-averaged rise velocity
-                post = lbm.lbm_postprocess(p, raw)
-                out[i].update(U_t=float(u[-1]), C_D=post["drag_coefficient"], steps=steps,
-                              converged=bool(steady or y > top))
-                done[i] = True
-                batch.set_active(i, False)
+    res = batch.run(window=window, rtol=rtol, max_steps=max_steps, top_margin=1.5)
     wall = time.perf_counter() - t0
+    out = []
+    for r in res:
+        finite = r["outcome"] != "diverged"
+        out.append(dict(U_t=r["rise_velocity"] if finite else math.nan,
+                        C_D=r["drag_coefficient"] if finite else math.nan, steps=r["steps_run"],
+                        converged=r["outcome"] in ("terminal", "top"), finite=finite, outcome=r["outcome"]))
     return out, wall
 
 
@@ -105,21 +78,15 @@ class TerminalStateModel:
         trusted = (~outside) & (spread[:, 0] < self.max_spread) & (spread[:, 1] < self.max_spread)
         return U, CD, trusted
 
-    def answer(self, cases, **run_kw):
+    def answer(self, cases, max_steps=40000, window=2000, rtol=0.05, stream=None):
         """Terminal states of cases: the network where trusted, the solver
-        elsewhere.  Returns (U_t, C_D, used_solver, wall seconds)."""
+        elsewhere, both inside the library (surr_answer).  Returns (U_t, C_D,
+        used_solver, wall seconds)."""
         X = np.stack([features(p, m) for p, _, m in cases])
         t0 = time.perf_counter()
-        U, CD, trusted = self.predict(X)
-        fallback = [c for c, t in zip(cases, trusted) if not t]
-        if fallback:
-            res, _ = run_to_terminal(fallback, **run_kw)
-            j = 0
-            for i, t in enumerate(trusted):
-                if not t:
-                    U[i], CD[i] = res[j]["U_t"], res[j]["C_D"]
-                    j += 1
-        return U, CD, ~trusted, time.perf_counter() - t0
+        y, used, _ = self.net.answer(X, [p for p, _, _ in cases], [b[0] for _, b, _ in cases],
+                                     max_spread=self.max_spread, window=window, rtol=rtol, max_steps=max_steps)
+        return y[:, 0], y[:, 1], used, time.perf_counter() - t0
 
 
 def evaluate(n_train=1024, n_test=128, grid=(100, 200), members=5, epochs=1000, max_steps=30000, seed=1000,

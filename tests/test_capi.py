@@ -56,12 +56,11 @@ def test_required_bytes_and_validation():
     assert lbm.lbm_required_bytes(dict(p, sigma12=1e-3, sigma13=1e-3, sigma23=3e-3)) == 0
     assert lbm.lbm_required_bytes(dict(p, tau_min=2.0, tau_max=1.0)) == 0
     assert lbm.lbm_required_bytes(dict(p, storage=7)) == 0
-    # FP16 storage of g rides on the collapsed form, and not in batches
+    # FP16 storage of g rides on the collapsed form, in batches too
     assert lbm.lbm_required_bytes(dict(p, storage=1)) == 0
     q = dict(p, storage=1, collapse_h=1)
     assert lbm.lbm_required_bytes(q) == lbm.lbm_required_bytes(dict(q, storage=0)) > 0
-    assert lbm.lbm_batch_required_bytes([q]) == 0
-    assert lbm.lbm_batch_required_bytes([dict(q, storage=0)]) > 0
+    assert lbm.lbm_batch_required_bytes([q]) == lbm.lbm_batch_required_bytes([dict(q, storage=0)]) > 0
     # open x boundaries: population state only, at least 4 columns, not batched
     o = dict(p, open_x=1, u_in=0.02)
     assert lbm.lbm_required_bytes(o) > 0

@@ -164,3 +164,67 @@ def test_persistent_batch_matches_oracle(lbm):
             ref = o64.field(n)
             err, floor = rel(batch.case(i).field(n), ref), rel(o32.field(n), ref)
             assert err <= max(1e-5, 4.0 * floor), (i, n, err, floor)
+
+
+def test_batch_run_to_terminal_matches_a_per_case_loop(lbm):
+    """lbm_batch_run (the terminal criterion and the window-averaged rise
+    velocity inside the library) against the same criterion written here
+    around single lattices stepped window by window."""
+    window, rtol, max_steps = 500, 0.02, 6000
+    cases = []
+    for i, (nx, ny) in enumerate([(48, 96), (40, 80), (56, 96)]):
+        p, _ = inputs.small_case(mobility=0, density_ratio=20.0 + 10 * i)
+        p = dict(p, nx=nx, ny=ny, pl_n=0.7 + 0.1 * i)
+        C = inputs.round_to_fp32(inputs.bubble_fields(nx, ny, 2, p["xi"], [(nx / 2, ny / 3, nx / 6, 3)], seed=i,
+                                                      noise=1e-8))
+        cases.append((p, C))
+    batch = lbm.Batch([p for p, _ in cases])
+    batch.set_persistent(True)
+    for i, (_, C) in enumerate(cases):
+        batch.case(i).set_fields(C)
+    res = batch.run(window=window, rtol=rtol, max_steps=max_steps, top_margin=1.5)
+    for i, (p, C) in enumerate(cases):
+        lat = lbm.Lattice(p)
+        lat.set_fields(C)
+        ob = lat.observables()
+        ys, top, steps = [ob["centroid"][1]], p["ny"] - 1 - 1.5 * ob["d_eq"], 0
+        while True:
+            lat.step(window)
+            steps += window
+            ob = lat.observables()
+            ys.append(ob["centroid"][1])
+            u = np.diff(ys) / window
+            if len(u) >= 3 and all(abs(u[-j] - u[-j - 1]) < rtol * abs(u[-j]) for j in (1, 2)):
+                outcome = "terminal"
+            elif ys[-1] > top:
+                outcome = "top"
+            elif steps >= max_steps:
+                outcome = "max_steps"
+            else:
+                continue
+            break
+        assert res[i]["outcome"] == outcome and res[i]["steps_run"] == steps, (i, res[i]["outcome"], outcome)
+        assert res[i]["rise_velocity"] == float(u[-1])
+        raw = np.array(ob["raw"])
+        raw[10] = u[-1] * raw[6]
+        assert res[i]["drag_coefficient"] == lbm.lbm_postprocess(p, raw)["drag_coefficient"]
+
+
+def test_fp16_batch_equals_fp16_single_lattices(lbm):
+    """FP16 storage of g (with the C state) in a persistent batch: the same
+    values as each case stepped alone in that form."""
+    cases = [(dict(p, collapse_h=1, storage=1), C) for p, C in _stable_cases()]
+    batch = lbm.Batch([p for p, _ in cases])
+    batch.set_persistent(True)
+    singles = []
+    for i, (p, C) in enumerate(cases):
+        batch.case(i).set_fields(C)
+        lat = lbm.Lattice(p)
+        lat.set_fields(C)
+        singles.append(lat)
+    batch.step(123)
+    for lat in singles:
+        lat.step(123)
+    for i, lat in enumerate(singles):
+        for n in ("C1", "p", "ux", "uy", "tau", "g"):
+            assert np.array_equal(batch.case(i).field(n), lat.field(n)), (i, n)
