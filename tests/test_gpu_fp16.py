@@ -138,3 +138,36 @@ def test_fp16_rising_bubble_error_report(lbm):
               "rise_velocity": 3e-3, "drag_coefficient": 4e-3, "centroid_y": 1e-3, "mass_liquid": 5e-6}
     bad = {k: report[k][0] for k, v in bounds.items() if not report[k][0] <= v}
     assert not bad, bad
+
+
+def test_fp16_terminal_velocity_against_the_oracle(lbm):
+    """The terminal rise velocity of Table 5 case 6 at density ratio 1000
+    (200 x 400) in the FP16 storage form (and in the FP32 collapsed form it
+    rides on), against the FP64 oracle's run to its terminal state
+    (tests/golden/oracle_terminal_table5_case6_r1000.json): window-averaged rise
+    velocity at the oracle's terminal step, and the drag coefficient from it.
+    The errors are printed; the bounds are about three times the measured ones."""
+    import json
+    import os
+
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "oracle_terminal_table5_case6_r1000.json")))
+    p, discs = inputs.table5_case(6, density_ratio=1000.0)
+    C = inputs.round_to_fp32(inputs.bubble_fields(p["nx"], p["ny"], 2, p["xi"], discs, seed=0, noise=1e-8))
+    every, window, k = gold["every"], gold["window"], gold["window"] // gold["every"]
+    errs = {}
+    for label, q in (("fp16", dict(p, collapse_h=1, storage=1)), ("collapsed fp32", dict(p, collapse_h=1))):
+        lat = lbm.Lattice(q)
+        lat.set_fields(C)
+        ys = []
+        for _ in range(gold["terminal_step"] // every):
+            lat.step(every)
+            ys.append(lat.observables()["centroid"][1])
+        u = np.diff(np.asarray(ys)[k - 1::k]) / window
+        raw = np.array(lat.observables()["raw"])
+        raw[10] = u[-1] * raw[6]
+        C_D = lbm.lbm_postprocess(p, raw)["drag_coefficient"]
+        errs[label] = (u[-1] / gold["U_t"] - 1.0, C_D / gold["C_D"] - 1.0)
+        print(f"{label}: U_t {u[-1]:.6e} ({errs[label][0]:+.2e} vs oracle), C_D {C_D:.4f} ({errs[label][1]:+.2e})")
+    assert abs(errs["collapsed fp32"][0]) < 0.005 and abs(errs["collapsed fp32"][1]) < 0.005
+    assert abs(errs["fp16"][0]) < 0.02 and abs(errs["fp16"][1]) < 0.02
