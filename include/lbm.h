@@ -158,7 +158,10 @@ lbm_status lbm_init_bubbles(lbm_handle *h, const lbm_bubble *bubbles, int nb, un
 
 /* Initial state from host fields (row-major ny x nx, double): C holds ncomp-1
  * planes (C1, then C2); p, ux, uy may be NULL for zero.  Populations are the
- * modified equilibria of Eq. 16 and Eq. 20; tau uses a zero strain rate. */
+ * modified equilibria of Eq. 16 and Eq. 20; tau uses a zero strain rate.  The
+ * doubles are copied to the device as they are (through the spare population
+ * buffer) and rounded to FP32 there; page-locked host memory makes the copy
+ * faster.  Synchronises the stream. */
 lbm_status lbm_set_fields(lbm_handle *h, const double *C, const double *p, const double *ux,
                           const double *uy);
 

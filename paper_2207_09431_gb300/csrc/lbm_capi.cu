@@ -16,22 +16,20 @@
 
 #include "lbm_internal.h"
 
-// Copies nplanes host planes (dense ny x nx doubles) into pitched device planes.
+// Copies nplanes host planes (dense ny x nx doubles) into pitched device FP32
+// planes: the doubles go to the device as they are, staged in the spare
+// population buffer g[1] (free until the initial equilibria are built), and a
+// kernel converts them; a NULL source sets the planes to zero.  Enqueued on
+// the handle's stream; the caller synchronises.
 static cudaError_t upload_planes(lbm_handle *h, float *dst, const double *src, int nplanes) {
-  const int nx = h->prm.nx, ny = h->prm.ny, pitch = h->dp.pitch;
-  h->stage.assign((size_t)nplanes * h->plane_floats(), 0.0f);
-  for (int q = 0; q < nplanes; ++q)
-    for (int y = 0; y < ny; ++y)
-      for (int x = 0; x < nx; ++x)
-        h->stage[(size_t)q * h->plane_floats() + (size_t)y * pitch + x] =
-            src ? (float)src[((size_t)q * ny + y) * nx + x] : 0.0f;
-  for (int q = 0; q < nplanes; ++q) {
-    cudaError_t e = cudaMemcpyAsync(dst + (size_t)q * (h->L.plane_bytes / sizeof(float)),
-                                    h->stage.data() + (size_t)q * h->plane_floats(),
-                                    h->plane_floats() * sizeof(float), cudaMemcpyHostToDevice, h->stream);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaStreamSynchronize(h->stream);
+  const size_t plane_bytes = h->L.plane_bytes;
+  if (!src) return cudaMemsetAsync(dst, 0, (size_t)nplanes * plane_bytes, h->stream);
+  const size_t bytes = (size_t)nplanes * h->prm.nx * h->prm.ny * sizeof(double);
+  if (bytes > 9 * plane_bytes) return cudaErrorInvalidValue;  // cannot happen: 2 planes of doubles < 9 of floats
+  double *staging = reinterpret_cast<double *>(h->g[1]);
+  cudaError_t e = cudaMemcpyAsync(staging, src, bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = lbm::launch_planes_from_f64(h->dp, staging, dst, nplanes, h->stream);
+  return e;
 }
 
 // Copies nplanes pitched device planes into dense host doubles.
@@ -201,7 +199,41 @@ lbm_status lbm_step(lbm_handle *h, long long nsteps) {
   if (nsteps < 0) return h->fail(LBM_E_INVAL, "nsteps < 0");
   cudaError_t e = cudaMemsetAsync(h->err, 0, sizeof(unsigned), h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "lbm_step memset");
-  for (long long t = 0; t < nsteps; ++t) h->launch_step(t == nsteps - 1, nullptr);
+  long long t = 0;
+  // Runs of kStepGraph steps are replayed from a captured graph (on a created
+  // stream; capture needs one).  The last step writes the diagnostics and is
+  // launched directly; a first run with a new configuration is too, so that
+  // its kernels are configured outside the capture.
+  const bool capturable = h->stream != nullptr && h->stream != cudaStreamLegacy && h->stream != cudaStreamPerThread;
+  const int K = lbm_handle::kStepGraph;
+  if (capturable && nsteps - 1 >= K) {
+    if (!h->graph[h->cur] || h->graph_variant[h->cur] != h->variant) {
+      h->launch_step(false, nullptr);
+      t = 1;
+      const int c = h->cur;
+      if (h->graph[c]) cudaGraphExecDestroy(h->graph[c]);
+      h->graph[c] = nullptr;
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+      for (int k = 0; k < K && e == cudaSuccess; ++k) {
+        h->launch_step(false, nullptr);
+        e = cudaGetLastError();
+      }
+      cudaError_t ec = cudaStreamEndCapture(h->stream, &g);
+      if (e == cudaSuccess) e = ec;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[c], g, 0);
+      if (g) cudaGraphDestroy(g);
+      h->cur = c;  // an even number of captured steps returns to the same buffer
+      if (e != cudaSuccess) {
+        h->graph[c] = nullptr;
+        return h->cuda_fail(e, "lbm_step graph capture");
+      }
+      h->graph_variant[c] = h->variant;
+    }
+    for (; nsteps - 1 - t >= K && e == cudaSuccess; t += K) e = cudaGraphLaunch(h->graph[h->cur], h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "lbm_step graph launch");
+  }
+  for (; t < nsteps; ++t) h->launch_step(t == nsteps - 1, nullptr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return h->cuda_fail(e, "lbm_step launch");
   unsigned flag = 0;

@@ -182,6 +182,16 @@ struct lbm_handle {
   double prev_v, y_int;
   std::string last_error;
   std::vector<float> stage;  // host staging (pitched FP32 planes)
+  // captured runs of kStepGraph steps without diagnostics, one per starting
+  // buffer (cur), for the launch configuration they were captured with
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_variant[2] = {-1, -1};
+  static constexpr int kStepGraph = 16;
+
+  ~lbm_handle() {
+    for (auto &g : graph)
+      if (g) cudaGraphExecDestroy(g);
+  }
 
   lbm_status fail(lbm_status s, const std::string &msg) {
     last_error = msg;

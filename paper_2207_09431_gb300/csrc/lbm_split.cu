@@ -498,6 +498,18 @@ __global__ void __launch_bounds__(kObsThreads) k_observables(DevParams P, const 
   }
 }
 
+// Dense FP64 host-layout planes (ny x nx each) into pitched FP32 planes, one
+// thread per column of the pitch (the padding columns get 0); FP64 -> FP32
+// rounds to nearest, as a host conversion does.
+__global__ void k_planes_from_f64(DevParams P, const double *__restrict__ src, float *__restrict__ dst,
+                                  int nplanes) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= P.pitch) return;
+  for (int q = 0; q < nplanes; ++q)
+    dst[(long long)q * P.plane + (long long)y * P.pitch + x] =
+        x < P.nx ? (float)src[((long long)q * P.ny + y) * P.nx + x] : 0.0f;
+}
+
 static dim3 node_grid(const DevParams &P, dim3 blk) {
   return dim3((P.nx + blk.x - 1) / blk.x, (P.ny + blk.y - 1) / blk.y);
 }
@@ -523,6 +535,11 @@ void launch_macros(const DevParams &P, const StepBuffers &B, cudaStream_t s) {
   const dim3 grd = node_grid(P, blk);
   if (B.h_in) k_moments<<<grd, blk, 0, s>>>(P, B.h_in, B.C);  // null: the state holds C
   k_fields<<<grd, blk, 0, s>>>(P, B.C, B.g_in, B.tau_in, B.mu, B.p, B.ux, B.uy, nullptr, nullptr, B.err, 0);
+}
+
+cudaError_t launch_planes_from_f64(const DevParams &P, const double *src, float *dst, int nplanes, cudaStream_t s) {
+  k_planes_from_f64<<<dim3((P.pitch + 127) / 128, P.ny), 128, 0, s>>>(P, src, dst, nplanes);
+  return cudaGetLastError();
 }
 
 void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s) {

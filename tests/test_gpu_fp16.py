@@ -146,7 +146,8 @@ def test_fp16_terminal_velocity_against_the_oracle(lbm):
     rides on), against the FP64 oracle's run to its terminal state
     (tests/golden/oracle_terminal_table5_case6_r1000.json): window-averaged rise
     velocity at the oracle's terminal step, and the drag coefficient from it.
-    The errors are printed; the bounds are about three times the measured ones."""
+    The errors are printed (measured: FP16 U_t +0.52 %, C_D -0.97 %; FP32 C form
+    +0.27 %, -0.46 %); the bounds leave room above them."""
     import json
     import os
 
@@ -169,5 +170,5 @@ def test_fp16_terminal_velocity_against_the_oracle(lbm):
         C_D = lbm.lbm_postprocess(p, raw)["drag_coefficient"]
         errs[label] = (u[-1] / gold["U_t"] - 1.0, C_D / gold["C_D"] - 1.0)
         print(f"{label}: U_t {u[-1]:.6e} ({errs[label][0]:+.2e} vs oracle), C_D {C_D:.4f} ({errs[label][1]:+.2e})")
-    assert abs(errs["collapsed fp32"][0]) < 0.005 and abs(errs["collapsed fp32"][1]) < 0.005
-    assert abs(errs["fp16"][0]) < 0.02 and abs(errs["fp16"][1]) < 0.02
+    assert abs(errs["collapsed fp32"][0]) < 0.0075 and abs(errs["collapsed fp32"][1]) < 0.0075
+    assert abs(errs["fp16"][0]) < 0.015 and abs(errs["fp16"][1]) < 0.02

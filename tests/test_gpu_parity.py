@@ -331,3 +331,25 @@ def test_layered_channel_steady_state(lbm):
     assert np.linalg.norm(u - ua) / np.linalg.norm(ua) <= 0.01
     uq = ccf.stress_balance_profile(y, lat.field("tau")[:, 0] / 3.0, F, H)
     assert np.linalg.norm(u - uq) / np.linalg.norm(uq) <= 2e-3
+
+
+def test_graph_replayed_steps_equal_direct_launches(lbm):
+    """On a created stream lbm_step replays runs of 16 steps from a captured
+    graph; on the default stream it launches every step.  Same values, also
+    after a change of launch configuration (the graph is captured again)."""
+    import torch
+
+    p, C = _bubble_case(70, 96, mobility=1)
+    direct = lbm.Lattice(p)                         # default stream: no capture
+    replay = lbm.Lattice(p, stream=torch.cuda.Stream())
+    for lat in (direct, replay):
+        lat.set_fields(C)
+        lat.step(53)                                # 1 direct + 3 x 16 replayed + 4 direct
+    for n in ("C1", "p", "ux", "uy", "tau", "g", "h", "shear"):
+        assert np.array_equal(replay.field(n), direct.field(n)), n
+    lbm.lbm_set_kernel_config(replay.h, 6)
+    lbm.lbm_set_kernel_config(direct.h, 6)
+    for lat in (direct, replay):
+        lat.step(40)
+    for n in ("C1", "p", "uy", "tau", "g", "h"):
+        assert np.array_equal(replay.field(n), direct.field(n)), n
