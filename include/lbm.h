@@ -288,7 +288,9 @@ enum { LBM_RUN_MAX_STEPS = 0, LBM_RUN_TERMINAL = 1, LBM_RUN_TOP = 2, LBM_RUN_DIV
 
 /* Runs every active, initialised case of the batch to its terminal state (the
  * cases advance together with lbm_batch_step, in the batch's current launch
- * mode, one window at a time; a case leaves the batch when it stops).  For
+ * mode, one window at a time; a case leaves the batch when it stops, and the
+ * launch configuration is tuned again, as by lbm_batch_autotune, whenever the
+ * set of running cases changes).  For
  * case i: outcome[i] is one of LBM_RUN_*, steps[i] (may be NULL) the steps it
  * ran, and out[i] its observables at the stop, with rise_velocity = U_t, the
  * window-averaged rise velocity of its last window (0 before a whole window),

@@ -8,6 +8,7 @@
 // use the single-lattice calls on lbm_batch_case(b, i).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <string>
@@ -86,9 +87,26 @@ struct lbm_batch {
       int tx = 32, ty = 8;
       lbm::batched_variant_tile(nh, v, &tx, &ty);
       const int ny = h[i]->dp.ny;
-      for (int y0 = 0; y0 < ny; y0 += ty)
-        for (int x0 = 0; x0 < h[i]->dp.nx; x0 += tx) w.push_back({i, x0, y0, y0 + ty < ny ? y0 + ty : ny});
+      if (lbm::batched_variant_is_sweep(nh, v)) {
+        // sweep segments: the rows of a strip split evenly (an even number of
+        // rows each, as the two-row pipeline steps take them), so that no
+        // short last segment pays a whole pipeline fill for a few rows
+        const int nseg = (ny + ty - 1) / ty;
+        int len = (ny + nseg - 1) / nseg;
+        len += len & 1;
+        for (int y0 = 0; y0 < ny; y0 += len)
+          for (int x0 = 0; x0 < h[i]->dp.nx; x0 += tx) w.push_back({i, x0, y0, y0 + len < ny ? y0 + len : ny});
+      } else {
+        for (int y0 = 0; y0 < ny; y0 += ty)
+          for (int x0 = 0; x0 < h[i]->dp.nx; x0 += tx) w.push_back({i, x0, y0, y0 + ty < ny ? y0 + ty : ny});
+      }
     }
+    // longest items first: the CTAs take items in order (one launch per step)
+    // or round robin (persistent launch), which then approximates the
+    // longest-processing-time schedule
+    std::stable_sort(w.begin(), w.end(), [](const lbm::WorkItem &a, const lbm::WorkItem &b) {
+      return a.y1 - a.y0 > b.y1 - b.y0;
+    });
     if (w.size() > work_cap) return cudaErrorInvalidValue;  // the arena's work list is sized for 32 x 8 items
     *count = (int)w.size();
     if (w.empty()) return cudaSuccess;
@@ -420,7 +438,15 @@ lbm_status lbm_batch_run(lbm_batch *b, const lbm_run_opts *opts, lbm_obs *out, i
     b->work_valid = false;
     --left;
   };
+  int tuned_for = -1;  // running cases when the launch configuration was last tuned
   while (left > 0) {
+    if (left != tuned_for) {
+      // the work list changed: pick the launch configuration for the cases
+      // still running (timed without advancing them)
+      lbm_status st = lbm_batch_autotune(b, 1, nullptr);
+      if (st != LBM_OK) return st;
+      tuned_for = left;
+    }
     lbm_status st = lbm_batch_step(b, opts->window);
     if (st != LBM_OK && st != LBM_E_DIVERGED) return st;
     for (int i = 0; i < n; ++i) {

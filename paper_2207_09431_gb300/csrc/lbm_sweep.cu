@@ -728,7 +728,9 @@ static cudaError_t sweep_persistent_dispatch(int v, const BatchCase *c, const Wo
   if constexpr (NH == 1) {
     switch (v) {
       case 2:
-      case 6: return launch_sweep_persistent_t<60, 2, NH, FORM, 160, 3>(c, w, n, parity0, nsteps, sync, lim, s, grid);
+      case 6:
+      case 7:
+      case 8: return launch_sweep_persistent_t<60, 2, NH, FORM, 160, 3>(c, w, n, parity0, nsteps, sync, lim, s, grid);
       case 3: return launch_sweep_persistent_t<64, 2, NH, FORM, 160, 3>(c, w, n, parity0, nsteps, sync, lim, s, grid);
       default: return launch_sweep_persistent_t<58, 2, NH, FORM, 128, 3>(c, w, n, parity0, nsteps, sync, lim, s, grid);
     }
@@ -738,12 +740,13 @@ static cudaError_t sweep_persistent_dispatch(int v, const BatchCase *c, const Wo
   }
 }
 
-int sweep_batched_count(int nh) { return nh == 1 ? 7 : 2; }
+int sweep_batched_count(int nh) { return nh == 1 ? 10 : 2; }
 
 // (strip width, segment rows): short segments give many work items for the
 // waves, long ones fewer pipeline fill steps per item
 void sweep_batched_shape(int nh, int v, int *tx, int *rows) {
-  static const int s1[7][2] = {{58, 48}, {58, 96}, {60, 48}, {64, 48}, {58, 64}, {58, 72}, {60, 64}};
+  static const int s1[10][2] = {{58, 48}, {58, 96}, {60, 48}, {64, 48}, {58, 64}, {58, 72}, {60, 64},
+                                {60, 128}, {60, 200}, {58, 160}};
   static const int s2[2][2] = {{64, 48}, {62, 48}};
   if (v < 0 || v >= sweep_batched_count(nh)) v = 0;
   *tx = nh == 1 ? s1[v][0] : s2[v][0];
@@ -756,7 +759,9 @@ static cudaError_t sweep_batched_dispatch(int v, const BatchCase *c, const WorkI
   if constexpr (NH == 1) {
     switch (v) {
       case 2:
-      case 6: return launch_sweep_batched_t<60, 2, NH, FORM, 160, 3>(c, w, n, parity, s);
+      case 6:
+      case 7:
+      case 8: return launch_sweep_batched_t<60, 2, NH, FORM, 160, 3>(c, w, n, parity, s);
       case 3: return launch_sweep_batched_t<64, 2, NH, FORM, 160, 3>(c, w, n, parity, s);
       default: return launch_sweep_batched_t<58, 2, NH, FORM, 128, 3>(c, w, n, parity, s);
     }

@@ -526,7 +526,6 @@ lbm_status surr_answer(surr_net *n, const double *X, const lbm_params *cases, co
   }
   for (size_t k = 0; k < fb.size() && st == LBM_OK; ++k)
     st = lbm_init_bubbles(lbm_batch_case(b, (int)k), &bubbles[fb[k]], 1, (unsigned long long)fb[k], noise_amp);
-  if (st == LBM_OK) st = lbm_batch_autotune(b, 2, nullptr);
   std::vector<lbm_obs> obs(fb.size());
   std::vector<int> outc(fb.size());
   if (st == LBM_OK) st = lbm_batch_run(b, opts, obs.data(), outc.data(), nullptr);
