@@ -228,3 +228,21 @@ def test_fp16_batch_equals_fp16_single_lattices(lbm):
     for i, lat in enumerate(singles):
         for n in ("C1", "p", "ux", "uy", "tau", "g"):
             assert np.array_equal(batch.case(i).field(n), lat.field(n)), (i, n)
+
+
+def test_batch_run_reports_diverged_and_step_limit_cases(lbm):
+    """A case that diverges (the R = 10 bubble at density ratio 1000) is an
+    outcome of lbm_batch_run, not an error: it stops as 'diverged' within its
+    first windows while the others run on, to the step limit here."""
+    p_bad, b_bad = inputs.small_case(density_ratio=1000.0)
+    p_ok, b_ok = inputs.small_case(density_ratio=20.0)
+    cases = [(p_ok, b_ok), (p_bad, b_bad), (dict(p_ok, pl_n=0.9), b_ok)]
+    batch = lbm.Batch([p for p, _ in cases])
+    batch.set_persistent(True)
+    for i, (p, b) in enumerate(cases):
+        batch.case(i).set_fields(inputs.bubble_fields(p["nx"], p["ny"], 2, p["xi"], b, seed=i, noise=1e-8))
+    res = batch.run(window=200, rtol=1e-9, max_steps=1000, top_margin=0.0)
+    assert res[1]["outcome"] == "diverged" and res[1]["steps_run"] <= 400
+    for i in (0, 2):
+        assert res[i]["outcome"] in ("max_steps", "top") and res[i]["steps_run"] <= 1000
+        assert np.isfinite(res[i]["rise_velocity"]) and np.isfinite(res[i]["drag_coefficient"])
