@@ -290,12 +290,12 @@ enum { LBM_RUN_MAX_STEPS = 0, LBM_RUN_TERMINAL = 1, LBM_RUN_TOP = 2, LBM_RUN_DIV
  * cases advance together with lbm_batch_step, in the batch's current launch
  * mode, one window at a time; a case leaves the batch when it stops, and the
  * launch configuration is tuned again, as by lbm_batch_autotune, whenever the
- * set of running cases changes).  For
- * case i: outcome[i] is one of LBM_RUN_*, steps[i] (may be NULL) the steps it
- * ran, and out[i] its observables at the stop, with rise_velocity = U_t, the
- * window-averaged rise velocity of its last window (0 before a whole window),
- * and drag_coefficient, Re and Mo recomputed from U_t (Eq. 37-40); cases that
- * were inactive or uninitialised get LBM_RUN_SKIPPED and are left unchanged.
+ * set of running cases changes).  For case i: outcome[i] is one of LBM_RUN_*,
+ * steps[i] (may be NULL) the steps it ran, and out[i] its observables at the
+ * stop, with rise_velocity = U_t, the window-averaged rise velocity of its last
+ * window (0 before a whole window), and drag_coefficient, Re and Mo recomputed
+ * from U_t (Eq. 37-40); cases that were inactive or uninitialised get
+ * LBM_RUN_SKIPPED and are left unchanged.
  * Cases that stopped stay inactive.  Returns LBM_E_INVAL for bad options,
  * LBM_E_TIMEOUT / LBM_E_CUDA as lbm_batch_step; a diverged case is an outcome,
  * not an error. */
