@@ -1,7 +1,7 @@
 """The surrogate pipeline end to end: terminal states of 1024 seeded 100 x 200
 rising-bubble cases from the batched solver, an ensemble of five networks
 trained on them by the library's kernels, and 128 held-out cases solved in
-full as the judge.  Shows what the network gains over the solver alone (time
+full as the yardstick.  Shows what the network gains over the solver alone (time
 to an answer) and at what error, and that the solver answers every case the
 network does not trust."""
 import numpy as np
