@@ -307,12 +307,17 @@ lbm_status lbm_postprocess(const lbm_params *p, const double raw[15], lbm_obs *o
 lbm_status lbm_observables(lbm_handle *h, lbm_obs *out) {
   if (!h || !out) return LBM_E_INVAL;
   if (!h->initialized) return h->fail(LBM_E_STATE, "observables before initial fields");
-  lbm_status st = compute_macros(h);
-  if (st != LBM_OK) return st;
-  cudaError_t e = cudaMemsetAsync(h->acc, 0, 16 * sizeof(double), h->stream);
+  // C planes (the state itself in the C forms), FP32 populations, then the
+  // sums with u computed per node; no macro-field planes are written
+  lbm::StepBuffers B = h->buffers(h->cur);
+  cudaError_t e = cudaSuccess;
+  const float *g = fp32_populations(h, &e);
+  if (e != cudaSuccess) return h->cuda_fail(e, "FP16 decode");
+  if (B.h_in) lbm::launch_moments(h->dp, B.h_in, B.C, h->stream);
+  e = cudaMemsetAsync(h->acc, 0, 16 * sizeof(double), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ext, 0x7f, 8 * sizeof(int), h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "observables memset");
-  lbm::launch_observables(h->dp, h->buffers(h->cur), h->prm.gas_comp, h->acc, h->ext, h->stream);
+  lbm::launch_observables_direct(h->dp, B.C, g, h->prm.gas_comp, h->acc, h->ext, h->stream);
   double acc[16];
   int ext[8];
   e = cudaGetLastError();

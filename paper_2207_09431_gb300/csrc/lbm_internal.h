@@ -13,6 +13,18 @@
 #include "lbm.h"
 #include "lbm_kernels.h"
 
+namespace lbm {
+// C_i of the population form into the C planes (Eq. 22).
+void launch_moments(const DevParams &P, const float *h, float *C, cudaStream_t s);
+// FP64 observable sums (masses, thresholded masses, sum C_g, C_g-weighted
+// position and velocity, extents of C_g > 0.5) from the C planes and the FP32
+// populations g, with u computed per node as the macro-field kernel computes
+// it; acc (11 doubles) and ext (4 ints: xmin, -xmax, ymin, -ymax) are
+// accumulated with atomics.
+void launch_observables_direct(const DevParams &P, const float *C, const float *g, int gas_comp, double *acc,
+                               int *ext, cudaStream_t s);
+}  // namespace lbm
+
 namespace lbm_detail {
 
 constexpr int kVersion = 100;  // 0.1.0

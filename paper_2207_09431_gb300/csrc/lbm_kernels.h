@@ -102,7 +102,5 @@ void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s);
 // nplanes dense FP64 planes (ny x nx each, device) into pitched FP32 planes
 // (plane stride P.plane floats).
 cudaError_t launch_planes_from_f64(const DevParams &P, const double *src, float *dst, int nplanes, cudaStream_t s);
-void launch_observables(const DevParams &P, const StepBuffers &B, int gas_comp, double *acc, int *ext,
-                        cudaStream_t s);
 
 }  // namespace lbm

@@ -147,22 +147,19 @@ __global__ void k_moments(DevParams P, const float *__restrict__ h, float *__res
   }
 }
 
-// rho, mu_1..3, u, p and (if write_tau) the new relaxation time and strain rate.
-__global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float *__restrict__ g,
-                         const float *__restrict__ tau_prev, float *__restrict__ mu, float *__restrict__ pf,
-                         float *__restrict__ uxf, float *__restrict__ uyf, float *__restrict__ tau_new,
-                         float *__restrict__ shear, unsigned *err, int write_tau) {
-  int x, y;
-  if (!node_of_thread(P, x, y)) return;
-  const long long k = node_index(P, x, y);
+// The fields of node (x, y) from the order parameters around it and its g
+// (Eq. 5, 22-24): C and rho at the node and its neighbours, grad C, lap C,
+// grad rho, mu_1..3, the forces, the moments of g and u.  Shared by k_fields
+// and the observables, so that both see the same velocity.
+__device__ __forceinline__ void fields_core(const DevParams &P, const float *__restrict__ Cf,
+                                            const float *__restrict__ g, int x, int y, long long k, NodeCtx &n,
+                                            float (&Cn)[9][3], float (&rn)[9], float (&ga)[9], float &m0) {
   CReader cr{Cf, P.plane, P.nh};
-  float Cn[9][3], rn[9];
   for (int a = 0; a < 9; ++a) {
     long long kk = shifted(P, x, y, ex(a), ey(a));
     cr.at(kk, Cn[a]);
     rn[a] = rho_of(P, Cn[a][0], Cn[a][1], Cn[a][2]);
   }
-  NodeCtx n;
   float lapC[3];
   for (int j = 0; j < 3; ++j) {
     n.C[j] = Cn[0][j];
@@ -191,7 +188,8 @@ __global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float 
   n.Fs[1] = n.mu[0] * n.gC[0][1] + n.mu[1] * n.gC[1][1] + n.mu[2] * n.gC[2][1];
   n.Fb[0] = P.force_x;
   n.Fb[1] = -n.rho * P.gravity;
-  float ga[9], m0 = 0.f, mx = 0.f, my = 0.f;
+  m0 = 0.f;
+  float mx = 0.f, my = 0.f;
   for (int a = 0; a < 9; ++a) {
     ga[a] = g[pop_index(k, a, 9)];
     m0 += ga[a];
@@ -200,6 +198,20 @@ __global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float 
   }
   n.ux = (3.0f * mx + 0.5f * (n.Fs[0] + n.Fb[0])) / n.rho;
   n.uy = (3.0f * my + 0.5f * (n.Fs[1] + n.Fb[1])) / n.rho;
+}
+
+// rho, mu_1..3, u, p and (if write_tau) the new relaxation time and strain rate.
+__global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float *__restrict__ g,
+                         const float *__restrict__ tau_prev, float *__restrict__ mu, float *__restrict__ pf,
+                         float *__restrict__ uxf, float *__restrict__ uyf, float *__restrict__ tau_new,
+                         float *__restrict__ shear, unsigned *err, int write_tau) {
+  int x, y;
+  if (!node_of_thread(P, x, y)) return;
+  const long long k = node_index(P, x, y);
+  CReader cr{Cf, P.plane, P.nh};
+  float Cn[9][3], rn[9], ga[9], m0;
+  NodeCtx n;
+  fields_core(P, Cf, g, x, y, k, n, Cn, rn, ga, m0);
   n.p = m0 + 0.5f * kCs2 * (n.ux * n.grho[0] + n.uy * n.grho[1]);
   for (int j = 0; j < 3; ++j) mu[(long long)j * P.plane + k] = n.mu[j];
   pf[k] = n.p;
@@ -434,39 +446,51 @@ __global__ void k_init(DevParams P, const float *__restrict__ Cf, const float *_
   tau[k] = tau_mix(P, n.C[0], n.C[1], n.C[2], tau1);
 }
 
-// FP64 observable sums of Sec. 3.1 and Eq. 43-44 over the current fields:
-// acc[0..10] = M1..3, M1..3 above 0.5, A, sum C_g x, sum C_g y, sum C_g ux,
-// sum C_g uy; ext[0..3] = xmin, -xmax, ymin, -ymax of C_g > 0.5 (atomicMin).
-// Observable sums (Sec. 3.1; Eq. 43-44 inputs) in FP64: each thread walks
-// rows (a block per row, grid-stride) accumulating its nodes, then warp
-// shuffles, one shared-memory pass per block and one atomic per block and
-// quantity.
+// Observable sums (Sec. 3.1; Eq. 43-44 inputs) in FP64: acc[0..10] = M1..3,
+// M1..3 above 0.5, A, sum C_g x, sum C_g y, sum C_g ux, sum C_g uy; ext[0..3] =
+// xmin, -xmax, ymin, -ymax of C_g > 0.5.  Each thread walks rows (a block per
+// row, grid-stride) accumulating its nodes, then warp shuffles, one
+// shared-memory pass per block and one atomic per block and quantity.
 constexpr int kObsThreads = 256;
 
-__global__ void __launch_bounds__(kObsThreads) k_observables(DevParams P, const float *__restrict__ Cf,
-                                                             const float *__restrict__ uxf,
-                                                             const float *__restrict__ uyf, int gas_comp,
-                                                             double *acc, int *ext) {
+// Dense FP64 host-layout planes (ny x nx each) into pitched FP32 planes, one
+// thread per column of the pitch (the padding columns get 0); FP64 -> FP32
+// rounds to nearest, as a host conversion does.
+__global__ void k_planes_from_f64(DevParams P, const double *__restrict__ src, float *__restrict__ dst,
+                                  int nplanes) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+  if (x >= P.pitch) return;
+  for (int q = 0; q < nplanes; ++q)
+    dst[(long long)q * P.plane + (long long)y * P.pitch + x] =
+        x < P.nx ? (float)src[((long long)q * P.ny + y) * P.nx + x] : 0.0f;
+}
+
+// The observable sums straight from the state: C from the C planes, u
+// computed at each node as k_fields computes it (fields_core), without
+// writing the macro fields.
+__global__ void __launch_bounds__(kObsThreads) k_obs_direct(DevParams P, const float *__restrict__ Cf,
+                                                            const float *__restrict__ g, int gas_comp,
+                                                            double *acc, int *ext) {
   double v[11];
   for (int q = 0; q < 11; ++q) v[q] = 0.0;
   int e[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
-  const CReader cr{Cf, P.plane, P.nh};
   for (int y = blockIdx.x; y < P.ny; y += gridDim.x) {
     for (int x = threadIdx.x; x < P.nx; x += blockDim.x) {
       const long long k = node_index(P, x, y);
-      float C[3];
-      cr.at(k, C);
+      NodeCtx n;
+      float Cn[9][3], rn[9], ga[9], m0;
+      fields_core(P, Cf, g, x, y, k, n, Cn, rn, ga, m0);
       for (int i = 0; i < 3; ++i) {
-        v[i] += C[i];
-        v[3 + i] += C[i] > 0.5f ? (double)C[i] : 0.0;
+        v[i] += n.C[i];
+        v[3 + i] += n.C[i] > 0.5f ? (double)n.C[i] : 0.0;
       }
-      const double cg = C[gas_comp - 1];
+      const double cg = n.C[gas_comp - 1];
       v[6] += cg;
       v[7] += cg * x;
       v[8] += cg * y;
-      v[9] += cg * uxf[k];
-      v[10] += cg * uyf[k];
-      if (C[gas_comp - 1] > 0.5f) {
+      v[9] += cg * n.ux;
+      v[10] += cg * n.uy;
+      if (n.C[gas_comp - 1] > 0.5f) {
         e[0] = min(e[0], x);
         e[1] = min(e[1], -x);
         e[2] = min(e[2], y);
@@ -496,18 +520,6 @@ __global__ void __launch_bounds__(kObsThreads) k_observables(DevParams P, const 
     for (int w = 0; w < kObsThreads / 32; ++w) m = min(m, se[w][q]);
     if (m != 0x7fffffff) atomicMin(&ext[q], m);
   }
-}
-
-// Dense FP64 host-layout planes (ny x nx each) into pitched FP32 planes, one
-// thread per column of the pitch (the padding columns get 0); FP64 -> FP32
-// rounds to nearest, as a host conversion does.
-__global__ void k_planes_from_f64(DevParams P, const double *__restrict__ src, float *__restrict__ dst,
-                                  int nplanes) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-  if (x >= P.pitch) return;
-  for (int q = 0; q < nplanes; ++q)
-    dst[(long long)q * P.plane + (long long)y * P.pitch + x] =
-        x < P.nx ? (float)src[((long long)q * P.ny + y) * P.nx + x] : 0.0f;
 }
 
 static dim3 node_grid(const DevParams &P, dim3 blk) {
@@ -547,10 +559,16 @@ void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s) {
   k_init<<<node_grid(P, blk), blk, 0, s>>>(P, B.C, B.p, B.ux, B.uy, B.g_out, B.h_out, B.tau_out);
 }
 
-void launch_observables(const DevParams &P, const StepBuffers &B, int gas_comp, double *acc, int *ext,
-                        cudaStream_t s) {
-  const int blocks = P.ny < 1216 ? P.ny : 1216;  // 8 per SM on 152 SMs, at most one per row
-  k_observables<<<blocks, kObsThreads, 0, s>>>(P, B.C, B.ux, B.uy, gas_comp, acc, ext);
+void launch_moments(const DevParams &P, const float *h, float *C, cudaStream_t s) {
+  const dim3 blk(32, 8);
+  k_moments<<<node_grid(P, blk), blk, 0, s>>>(P, h, C);
 }
+
+void launch_observables_direct(const DevParams &P, const float *C, const float *g, int gas_comp, double *acc,
+                               int *ext, cudaStream_t s) {
+  const int blocks = P.ny < 1216 ? P.ny : 1216;  // 8 per SM on 152 SMs, at most one per row
+  k_obs_direct<<<blocks, kObsThreads, 0, s>>>(P, C, g, gas_comp, acc, ext);
+}
+
 
 }  // namespace lbm
