@@ -535,3 +535,39 @@ def test_bf16_rounding_reference_values():
     vals = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -9, np.float32(np.pi), -2.5, 1.0 + 2.0 ** -7 + 2.0 ** -8])
     want = np.array([1.0, 1.0, 1.0 + 2.0 ** -7, 3.140625, -2.5, 1.0 + 2.0 ** -6])
     assert np.array_equal(mlp.round_bf16(vals), want)
+
+
+def test_table5_inputs_are_the_printed_values():
+    """The Table 5 set-ups the density-ratio-1000 tests run are the printed
+    (n, k, g, sigma) of Sec. 4.3 (the golden file transcribes the tables)."""
+    table = {c["case"]: c for c in _golden("paper_tables5to7_bubble.json")["cases"]}
+    for case, (n, k, g, sigma) in inputs.TABLE5.items():
+        assert (n, k, g, sigma) == (table[case]["n"], table[case]["k"], table[case]["g"], table[case]["sigma"])
+        p, discs = inputs.table5_case(case)
+        assert (p["nx"], p["ny"]) == (200, 400) and discs == [(100.0, 120.0, 25.0, 3)]
+        assert p["rho"][2] == pytest.approx(1.0 / 800.0) and p["tau"][2] == 0.5
+
+
+def test_oracle_terminal_golden_is_self_consistent():
+    """The stored oracle rise to the terminal state: U_t is the last 2000-step
+    window of the stored centroid series, the 1 % rule holds there and not a
+    window earlier, and C_D is Eq. 37 at U_t through the oracle's
+    post-processing (the drag of a rising bubble: 4 (rho_l - rho_g) g d /
+    (3 rho_l U^2) with d from the gas area)."""
+    gold = _golden("oracle_terminal_table5_case6_r1000.json")
+    k = gold["window"] // gold["every"]
+    assert gold["steps"][-1] == gold["terminal_step"]
+    y = np.asarray(gold["ybar"])[k - 1::k]
+    u = np.diff(y) / gold["window"]
+    assert u[-1] == pytest.approx(gold["U_t"], rel=1e-12)
+
+    def terminal(v):
+        return len(v) >= 3 and all(abs(v[-j] - v[-j - 1]) < 0.01 * abs(v[-j]) for j in (1, 2))
+
+    assert terminal(u) and not terminal(u[:-1])
+    p, _ = inputs.table5_case(6, density_ratio=1000.0)
+    A = gold["area"][-1]
+    d = 2.0 * math.sqrt(A / math.pi)
+    rho_l, rho_g = p["rho"][0], p["rho"][2]
+    cd = 4.0 * (rho_l - rho_g) * p["gravity"] * d / (3.0 * rho_l * gold["U_t"] ** 2)
+    assert gold["C_D"] == pytest.approx(cd, rel=1e-9)
