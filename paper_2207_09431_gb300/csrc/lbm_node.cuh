@@ -67,6 +67,28 @@ __device__ __forceinline__ float iso_lap(const float (&v)[9]) {
   return fmaf(6.0f * LBM_W2, sd, (6.0f * LBM_W1) * sa);
 }
 
+// Packed FP32 forms (two lanes per instruction on sm_100-family SMs) of the
+// stencils above, for two fields stored side by side: each lane performs the
+// scalar helpers' operations in their order, so the values are theirs.
+__device__ __forceinline__ float2 bcast2(float v) { return make_float2(v, v); }
+// a - b with one rounding (the product by -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bcast2(-1.0f), a); }
+
+// pair differences, isotropic gradient and isotropic Laplacian of both lanes
+__device__ __forceinline__ void stencil2(const float2 (&v)[9], float2 (&D)[4], float2 &gx, float2 &gy,
+                                         float2 &lap) {
+  D[0] = sub2(v[1], v[3]);
+  D[1] = sub2(v[2], v[4]);
+  D[2] = sub2(v[5], v[7]);
+  D[3] = sub2(v[6], v[8]);
+  gx = __ffma2_rn(bcast2(3.0f * LBM_W2), sub2(D[2], D[3]), __fmul2_rn(bcast2(3.0f * LBM_W1), D[0]));
+  gy = __ffma2_rn(bcast2(3.0f * LBM_W2), __fadd2_rn(D[2], D[3]), __fmul2_rn(bcast2(3.0f * LBM_W1), D[1]));
+  const float2 v0 = v[0];
+  const float2 sa = __fadd2_rn(__fadd2_rn(sub2(v[1], v0), sub2(v[3], v0)), __fadd2_rn(sub2(v[2], v0), sub2(v[4], v0)));
+  const float2 sd = __fadd2_rn(__fadd2_rn(sub2(v[5], v0), sub2(v[7], v0)), __fadd2_rn(sub2(v[6], v0), sub2(v[8], v0)));
+  lap = __ffma2_rn(bcast2(6.0f * LBM_W2), sd, __fmul2_rn(bcast2(6.0f * LBM_W1), sa));
+}
+
 // e_a . (vx, vy) for a != 0.
 __device__ __forceinline__ float edot(int a, float vx, float vy) {
   const float sx = ex(a) > 0 ? vx : -vx, sy = ey(a) > 0 ? vy : -vy;
@@ -169,18 +191,36 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
   // Differences across the node along the direction pairs: the central
   // directional derivative d_a v = (v(x + e_a) - v(x - e_a)) / 2 is half of
   // one, and d_opp(a) v = -d_a v.
-  float Dp[4];
-  pair_diff(pn, Dp);
+  float Dp[4], px, py, mgxs[NH], mgys[NH], lapmus[NH];
+  if constexpr (NH == 1) {
+    // mu_1 and p side by side
+    float2 v[9], D[4], gx, gy, lp;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = make_float2(mun[0][a], pn[a]);
+    stencil2(v, D, gx, gy, lp);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Dp[k] = D[k].y;
+    px = gx.y;
+    py = gy.y;
+    mgxs[0] = gx.x;
+    mgys[0] = gy.x;
+    lapmus[0] = lp.x;
+  } else {
+    pair_diff(pn, Dp);
+    iso_grad(Dp, px, py);
+#pragma unroll
+    for (int i = 0; i < NH; ++i) {
+      float Dm[4];
+      pair_diff(mun[i], Dm);
+      iso_grad(Dm, mgxs[i], mgys[i]);
+      lapmus[i] = iso_lap(mun[i]);
+    }
+  }
   const float (&Dr)[4] = c.Dr;
-  float px, py;
-  iso_grad(Dp, px, py);
   float Fsx, Fsy, Cc[NH], kh[NH], hb[NH], hdmu[NH];
 #pragma unroll
   for (int i = 0; i < NH; ++i) {
-    float Dm[4], mgx, mgy;
-    pair_diff(mun[i], Dm);
-    iso_grad(Dm, mgx, mgy);
-    const float lapmu = iso_lap(mun[i]);
+    const float mgx = mgxs[i], mgy = mgys[i], lapmu = lapmus[i];
     const float gcx = c.gCx[i], gcy = c.gCy[i];
     Fsx = i == 0 ? c.dmu[0] * gcx : fmaf(c.dmu[i], gcx, Fsx);
     Fsy = i == 0 ? c.dmu[0] * gcy : fmaf(c.dmu[i], gcy, Fsy);
@@ -217,39 +257,50 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
   // X_a, d_a and e.u change sign between opposite directions, (e.u)^2 does
   // not: each is formed once per pair.  C_i Gamma_a is kept as its own term so
   // that the small corrections are not rounded into a value of the size of C_i.
-  float fn[9], eqf[9];
-  auto direction = [&](int a, float G, float E, float t, float ep, const float (&hq)[NH]) {
-    const float w = wt(a);
-    const float Gw = G - w;
-    const float ph = fmaf(t, Gw, E * G);
-    const float geq = fmaf(-0.5f, ph, fmaf(rcs2, Gw, w * p));
-    fn[a] = g[a] - geq;
-    eqf[a] = geq + ph;
+  // A direction and its opposite are evaluated as one pair on the packed FP32
+  // pipe (lane x: a, lane y: opp(a)), each lane the same operation sequence
+  // as the scalar form, so the values do not depend on the packing.
+  const float G0 = LBM_W0 * S0, Gw0 = G0 - LBM_W0;
+  const float ph0 = fmaf(-udr3, Gw0, -uF * G0);
+  const float geq0 = fmaf(-0.5f, ph0, fmaf(rcs2, Gw0, LBM_W0 * p));
+  const float fn0 = g[0] - geq0, eq0 = geq0 + ph0;
 #pragma unroll
-    for (int i = 0; i < NH; ++i) hs[i][a] = fmaf(Cc[i], G, G * fmaf(-kh[i], ep, hq[i]));
-  };
-  direction(0, LBM_W0 * S0, -uF, -udr3, c0, hb);
+  for (int i = 0; i < NH; ++i) hs[i][0] = fmaf(Cc[i], G0, G0 * fmaf(-kh[i], c0, hb[i]));
+  float2 fn2[4], eq2[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const int a = pair_dir(k);
+    const int a = pair_dir(k), b = opp(a);
     const float w = wt(a), eu = edot(a, ux, uy);
     const float wB = fmaf((4.5f * w) * eu, eu, w * S0);
     float X = edot(a, P.force_x, Fby);
 #pragma unroll
     for (int i = 0; i < NH; ++i) X = fmaf(hdmu[i], c.DC[i][k], X);
     const float o = fmaf(0.5f, Dp[k], -X);
-    float hqa[NH], hqb[NH];
+    const float2 G = __ffma2_rn(make_float2(3.0f * w, -3.0f * w), bcast2(eu), bcast2(wB));
+    const float2 E = __fadd2_rn(make_float2(X, -X), bcast2(-uF));
+    const float2 t = __ffma2_rn(make_float2(0.5f * kCs2, -0.5f * kCs2), bcast2(Dr[k]),
+                                bcast2(-udr3));
+    const float2 ep = __fadd2_rn(make_float2(o, -o), bcast2(c0));
+    const float2 Gw = __fadd2_rn(G, bcast2(-w));
+    const float2 ph = __ffma2_rn(t, Gw, __fmul2_rn(E, G));
+    const float wp = w * p;
+    const float2 geq = __ffma2_rn(bcast2(-0.5f), ph,
+                                  __ffma2_rn(bcast2(rcs2), Gw, bcast2(wp)));
+    fn2[k] = __ffma2_rn(geq, bcast2(-1.0f), make_float2(g[a], g[b]));  // g - geq, exact negation
+    eq2[k] = __fadd2_rn(geq, ph);
 #pragma unroll
     for (int i = 0; i < NH; ++i) {
-      hqa[i] = fmaf(0.25f, c.DC[i][k], hb[i]);
-      hqb[i] = fmaf(-0.25f, c.DC[i][k], hb[i]);
+      const float2 hq = __ffma2_rn(make_float2(0.25f, -0.25f), bcast2(c.DC[i][k]),
+                                   bcast2(hb[i]));
+      const float2 r = __ffma2_rn(bcast2(Cc[i]), G,
+                                  __fmul2_rn(G, __ffma2_rn(bcast2(-kh[i]), ep, hq)));
+      hs[i][a] = r.x;
+      hs[i][b] = r.y;
     }
-    direction(a, fmaf(3.0f * w, eu, wB), X - uF, fmaf(0.5f * kCs2, Dr[k], -udr3), o + c0, hqa);
-    direction(opp(a), fmaf(-3.0f * w, eu, wB), -X - uF, fmaf(-0.5f * kCs2, Dr[k], -udr3), c0 - o, hqb);
   }
   // second moments of the non-equilibrium part (pairs 5-7 and 6-8 enter all three)
-  const float s57 = fn[5] + fn[7], s68 = fn[6] + fn[8], sd = s57 + s68;
-  const float Pxx = (fn[1] + fn[3]) + sd, Pyy = (fn[2] + fn[4]) + sd, Pxy = s57 - s68;
+  const float s57 = fn2[2].x + fn2[2].y, s68 = fn2[3].x + fn2[3].y, sd = s57 + s68;
+  const float Pxx = (fn2[0].x + fn2[0].y) + sd, Pyy = (fn2[1].x + fn2[1].y) + sd, Pxy = s57 - s68;
   // (1/cs^2) (2 tau / (2 tau + 1)) / (2 tau rho cs^2) = 9 / ((2 tau + 1) rho)
   const float fac = __fdividef(9.0f * irho, 2.0f * tau_prev + 1.0f);
   const float Dxx = -fac * Pxx, Dyy = -fac * Pyy, Dxy = -fac * Pxy;
@@ -258,9 +309,14 @@ __device__ __forceinline__ void node_collide(const DevParams &P, const NodeCente
   const float tau1 = P.powerlaw ? tau_powerlaw_sq(P, gd2, irho) : P.tau[0];
   if constexpr (NH == 1) tn = tau_mix2(P, Cc[0], tau1);
   else tn = tau_mix(P, Cc[0], Cc[1], 1.0f - Cc[0] - Cc[1], tau1);
-  const float om = __fdividef(1.0f, tn + 0.5f);
+  const float om = __fdividef(1.0f, tn + 0.5f), om1 = 1.0f - om;
+  g[0] = fmaf(om1, fn0, eq0);
 #pragma unroll
-  for (int a = 0; a < 9; ++a) g[a] = (1.0f - om) * fn[a] + eqf[a];
+  for (int k = 0; k < 4; ++k) {
+    const float2 r = __ffma2_rn(make_float2(om1, om1), fn2[k], eq2[k]);
+    g[pair_dir(k)] = r.x;
+    g[opp(pair_dir(k))] = r.y;
+  }
 }
 
 // FP16 deviation codec of the FP16 storage form: g_a is kept as
