@@ -478,8 +478,9 @@ def run_batched(args, torch, dev, stream, rank=0, world=1, dist=None):
     one case after another on its own lattice (lbm_step), the latter on every
     eighth case.  Cases/hour = cases run to a stop per wall-clock hour.  Both
     forms compute the same node values, so their terminal velocities agree
-    (checked on the shared cases).  With several ranks every rank takes its
-    share of the cases and the times are the slowest rank's."""
+    (checked on the shared cases).  The C state form and FP16 g storage run
+    the same ensemble too (state_forms).  With several ranks every rank takes
+    its share of the cases and the times are the slowest rank's."""
     from paper_2207_09431_gb300 import lbm
 
     window, rtol, max_steps = 2000, 0.05, 40000
@@ -530,6 +531,8 @@ def run_batched(args, torch, dev, stream, rank=0, world=1, dist=None):
     same = [abs(u / res[i]["rise_velocity"] - 1.0) for (u, _, o), i in zip(single, sub)
             if o != "diverged" and res[i]["outcome"] != "diverged" and res[i]["rise_velocity"] != 0.0]
     step_bytes = step_bytes_per_node(1)
+    forms = {key: _batched_form(lbm, torch, dev, stream, cases, res, extra, K, window, rtol, max_steps, nodes, dist)
+             for key, extra in (("collapsed", {"collapse_h": 1}), ("fp16_storage", {"collapse_h": 1, "storage": 1}))}
     return {"cases": len(all_cases), "nodes": nodes, "ranks": world, "density_ratio": 1000.0,
             "mode": "persistent cooperative launches of up to 4096 steps, whole launches replayed from a CUDA graph",
             "ms_per_step": round(ms_batch, 4), "mlups": round(nodes / (ms_batch * 1e3), 1),
@@ -543,6 +546,56 @@ def run_batched(args, torch, dev, stream, rank=0, world=1, dist=None):
                          "cases_per_hour": round(stopped_single / wall_single * 3600.0, 1),
                          "max_rel_diff_U_t_vs_batched": max(same) if same else None},
             "speedup_cases_per_hour": round((stopped / wall_batch) / max(stopped_single / wall_single, 1e-12), 2),
+            "kernel_config": chosen, "state_forms": forms}
+
+
+def _batched_form(lbm, torch, dev, stream, cases, res32, extra, K, window, rtol, max_steps, nodes, dist):
+    """The same ensemble in a C state form (collapse_h = 1, 88 B per node-step)
+    or with FP16 g storage on it (60 B): kernel view over K persistent steps,
+    then every case run to its terminal state from fresh initial states; U_t
+    against the FP32 population batch on the cases that stop in both."""
+    batch = lbm.Batch([dict(c[0], **extra) for c in cases], device=dev, stream=stream)
+    batch.set_persistent(True)
+
+    def init():
+        for i, (p, b, _) in enumerate(cases):
+            batch.set_active(i, True)
+            batch.case(i).set_fields(inputs.bubble_fields(p["nx"], p["ny"], 2, p["xi"], b, seed=i, noise=1e-8))
+
+    init()
+    chosen = batch.autotune(reps=3)
+    batch.step(2)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    try:
+        batch.step(K)
+    except lbm.LbmError as err:
+        if err.status != -4:
+            raise
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = replicas.job_time_ms(ev0.elapsed_time(ev1) / K, dist)
+    init()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    res = batch.run(window=window, rtol=rtol, max_steps=max_steps, top_margin=1.5)
+    torch.cuda.synchronize(dev)
+    wall = replicas.job_time_ms((time.perf_counter() - t0) * 1e3, dist) / 1e3
+    outcomes = {}
+    for r in res:
+        outcomes[r["outcome"]] = outcomes.get(r["outcome"], 0) + 1
+    stops = ("terminal", "top")
+    d = [abs(r["rise_velocity"] / r32["rise_velocity"] - 1.0) for r, r32 in zip(res, res32)
+         if r["outcome"] in stops and r32["outcome"] in stops and r32["rise_velocity"] != 0.0]
+    bpn = 2 * (9 * 2 + 4 + 4 + 4) if extra.get("storage") else 4 * 2 * (9 + 1 + 1)
+    del batch
+    return {"bytes_per_node": bpn, "ms_per_step": round(ms, 4), "mlups": round(nodes / (ms * 1e3), 1),
+            "outcomes": outcomes, "wall_s_to_terminal": round(wall, 2),
+            "cases_per_hour": round((len(cases) - outcomes.get("diverged", 0)) / wall * 3600.0, 1),
+            "U_t_rel_diff_vs_fp32_populations": {
+                "cases": len(d), "median": float(np.median(d)) if d else None,
+                "p90": float(np.percentile(d, 90)) if d else None, "max": max(d) if d else None},
             "kernel_config": chosen}
 
 
