@@ -335,6 +335,29 @@ lbm_status surr_forward_backward(surr_net *n, int member, const double *X, const
  * training hull.  final_loss (may be NULL): loss of the last mini-batch. */
 lbm_status surr_train(surr_net *n, const double *X, const double *Y, int rows, int epochs, int batch, double lr,
                       unsigned long long seed, double *final_loss);
+/* surr_train with a local reliability estimate: the rows are dealt into
+ * `folds` (2..16) groups by a permutation drawn from `seed`; for each group the
+ * ensemble is trained from init_weights (members x surr_param_count() doubles,
+ * as for surr_create; Adam restarted) on the other groups and predicts the
+ * group's rows, and each row keeps its out-of-fold residual, the larger of
+ * |prediction - target| over the two outputs (relative errors, as the outputs
+ * are logarithms).  Then the ensemble is trained on every row as surr_train
+ * does (final_loss as there).  The rows and residuals are kept (host memory)
+ * for surr_local_residual.  Costs folds + 1 trainings. */
+lbm_status surr_train_cv(surr_net *n, const double *X, const double *Y, int rows, int folds, int epochs, int batch,
+                         double lr, unsigned long long seed, const double *init_weights, double *final_loss);
+/* For each of rows x 5 raw inputs, the largest out-of-fold residual among the
+ * k training rows nearest to it (Euclidean distance in inputs standardised by
+ * the training set's mean and standard deviation; ties by row order): a
+ * measure of how well the ensemble predicts the labels around that input when
+ * they were held out, including the scatter of the labels themselves, which
+ * the members' disagreement does not see.  LBM_E_STATE before surr_train_cv;
+ * LBM_E_INVAL unless 1 <= k <= training rows. */
+lbm_status surr_local_residual(surr_net *n, const double *X, int rows, int k, double *local);
+/* Makes surr_answer also require surr_local_residual(k) < max_residual for a
+ * case to be trusted; max_residual <= 0 turns the test off (the default).
+ * LBM_E_INVAL for k < 1. */
+lbm_status surr_set_local_trust(surr_net *n, int k, double max_residual);
 /* Ensemble mean and disagreement (the largest deviation of one member from
  * the mean) of the two outputs for rows x 5 raw inputs; outside[r] = 1 when
  * input r lies outside the training box.  y_spread and outside may be NULL. */
@@ -342,9 +365,11 @@ lbm_status surr_predict(surr_net *n, const double *X, int rows, double *y_mean, 
 /* Terminal rise velocity and drag coefficient (Sec. 4.3, Eq. 37) of `rows`
  * rising-bubble cases, from the network where the case is trusted and from the
  * lattice Boltzmann solver (the fallback) elsewhere.  Trusted: the features
- * X[r] (rows x 5, as for surr_predict) lie inside the training box and every
+ * X[r] (rows x 5, as for surr_predict) lie inside the training box, every
  * member lies within max_spread of the ensemble mean in both outputs, which are
- * (log U_t, log C_D) as the caller trained them.  The untrusted cases are set
+ * (log U_t, log C_D) as the caller trained them, and, when surr_set_local_trust
+ * has set a bound after surr_train_cv, the local residual lies below it.  The
+ * untrusted cases are set
  * up from cases[r] and bubbles[r] (one disc each; lbm_init_bubbles with seed r
  * and noise_amp), advanced together as one batch carved from dev_arena (at
  * least lbm_batch_required_bytes of those cases; every case must suit a batch)

@@ -13,11 +13,13 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "lbm.h"
@@ -181,6 +183,11 @@ struct surr_net {
   double in_mean[5] = {0}, in_std[5] = {1, 1, 1, 1, 1}, out_mean[2] = {0}, out_std[2] = {1, 1};
   double lo[5] = {0}, hi[5] = {0};
   bool trained = false;
+  // out-of-fold residuals of the training rows (surr_train_cv) and the
+  // local-trust bound of surr_answer
+  std::vector<double> cv_x, cv_res;
+  int trust_k = 0;
+  double trust_max = 0.0;
   long long adam_t[16] = {0};
   std::string last_error;
 
@@ -367,6 +374,8 @@ lbm_status surr_train(surr_net *n, const double *X, const double *Y, int rows, i
     return LBM_E_INVAL;
   batch = batch > rows ? rows : batch;
   if (batch > n->max_batch) return LBM_E_INVAL;
+  n->cv_x.clear();  // out-of-fold residuals belong to the set they were computed on
+  n->cv_res.clear();
   for (int c = 0; c < 5; ++c) {
     double s = 0, s2 = 0, lo = X[c], hi = X[c];
     for (int r = 0; r < rows; ++r) {
@@ -442,6 +451,99 @@ lbm_status surr_train(surr_net *n, const double *X, const double *Y, int rows, i
   return LBM_OK;
 }
 
+// Restores the initial weights of every member and restarts Adam.
+static lbm_status surr_reset(surr_net *n, const double *init_weights) {
+  std::vector<float> w((size_t)n->members * kParams);
+  for (size_t i = 0; i < w.size(); ++i) w[i] = (float)init_weights[i];
+  cudaError_t e = cudaMemcpyAsync(n->w, w.data(), w.size() * 4, cudaMemcpyHostToDevice, n->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->m, 0, w.size() * 4, n->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, w.size() * 4, n->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+  if (e != cudaSuccess) return n->cuda_fail(e, "surr_reset");
+  for (long long &t : n->adam_t) t = 0;
+  n->trained = false;
+  return LBM_OK;
+}
+
+lbm_status surr_train_cv(surr_net *n, const double *X, const double *Y, int rows, int folds, int epochs, int batch,
+                         double lr, unsigned long long seed, const double *init_weights, double *final_loss) {
+  if (!n || !X || !Y || !init_weights || rows < folds || folds < 2 || folds > 16 || rows > n->max_rows)
+    return LBM_E_INVAL;
+  // fold of each row: position in a seeded permutation, modulo folds
+  std::vector<int> perm(rows), fold(rows);
+  for (int r = 0; r < rows; ++r) perm[r] = r;
+  uint64_t st = seed ^ 0x5DEECE66DULL;
+  for (int r = rows - 1; r > 0; --r) std::swap(perm[r], perm[(int)(sm64(st) % (uint64_t)(r + 1))]);
+  for (int i = 0; i < rows; ++i) fold[perm[i]] = i % folds;
+  std::vector<double> res(rows, 0.0);
+  for (int f = 0; f < folds; ++f) {
+    std::vector<double> xt, yt, xv;
+    std::vector<int> rv;
+    for (int r = 0; r < rows; ++r) {
+      if (fold[r] == f) {
+        rv.push_back(r);
+        xv.insert(xv.end(), X + 5 * r, X + 5 * r + 5);
+      } else {
+        xt.insert(xt.end(), X + 5 * r, X + 5 * r + 5);
+        yt.insert(yt.end(), Y + 2 * r, Y + 2 * r + 2);
+      }
+    }
+    lbm_status s = surr_reset(n, init_weights);
+    if (s == LBM_OK) s = surr_train(n, xt.data(), yt.data(), (int)(xt.size() / 5), epochs, batch, lr, seed + f + 1, nullptr);
+    if (s != LBM_OK) return s;
+    const int nv = (int)rv.size();
+    std::vector<double> mean((size_t)nv * 2);
+    for (int r0 = 0; r0 < nv; r0 += n->max_batch) {
+      const int m = nv - r0 < n->max_batch ? nv - r0 : n->max_batch;
+      s = surr_predict(n, xv.data() + 5 * r0, m, mean.data() + 2 * r0, nullptr, nullptr);
+      if (s != LBM_OK) return s;
+    }
+    for (int i = 0; i < nv; ++i) {
+      const int r = rv[i];
+      res[r] = std::fmax(std::fabs(mean[2 * i] - Y[2 * r]), std::fabs(mean[2 * i + 1] - Y[2 * r + 1]));
+    }
+  }
+  lbm_status s = surr_reset(n, init_weights);
+  if (s == LBM_OK) s = surr_train(n, X, Y, rows, epochs, batch, lr, seed, final_loss);
+  if (s != LBM_OK) return s;
+  n->cv_x.assign(X, X + 5 * (size_t)rows);
+  n->cv_res = res;
+  return LBM_OK;
+}
+
+lbm_status surr_local_residual(surr_net *n, const double *X, int rows, int k, double *local) {
+  if (!n || !X || !local || rows < 0) return LBM_E_INVAL;
+  const int nt = (int)n->cv_res.size();
+  if (nt == 0 || !n->trained) {
+    n->last_error = "surr_local_residual before surr_train_cv";
+    return LBM_E_STATE;
+  }
+  if (k < 1 || k > nt) return LBM_E_INVAL;
+  std::vector<std::pair<double, int>> d(nt);
+  for (int r = 0; r < rows; ++r) {
+    for (int t = 0; t < nt; ++t) {
+      double s = 0.0;
+      for (int c = 0; c < 5; ++c) {
+        const double z = (X[5 * r + c] - n->cv_x[5 * (size_t)t + c]) / n->in_std[c];
+        s += z * z;
+      }
+      d[t] = {s, t};
+    }
+    std::partial_sort(d.begin(), d.begin() + k, d.end());
+    double m = 0.0;
+    for (int i = 0; i < k; ++i) m = std::fmax(m, n->cv_res[d[i].second]);
+    local[r] = m;
+  }
+  return LBM_OK;
+}
+
+lbm_status surr_set_local_trust(surr_net *n, int k, double max_residual) {
+  if (!n || k < 1) return LBM_E_INVAL;
+  n->trust_k = k;
+  n->trust_max = max_residual;
+  return LBM_OK;
+}
+
 // Ensemble prediction: mean and disagreement (largest deviation of a member
 // from the mean) of the two outputs in raw units, and flags for inputs outside
 // the training box.
@@ -496,9 +598,16 @@ lbm_status surr_answer(surr_net *n, const double *X, const lbm_params *cases, co
   std::vector<int> outside(rows);
   lbm_status st = surr_predict(n, X, rows, mean.data(), spread.data(), outside.data());
   if (st != LBM_OK) return st;
+  const bool local_test = n->trust_max > 0.0;
+  std::vector<double> local(rows, 0.0);
+  if (local_test) {
+    st = surr_local_residual(n, X, rows, n->trust_k, local.data());
+    if (st != LBM_OK) return st;
+  }
   std::vector<int> fb;
   for (int r = 0; r < rows; ++r) {
-    const bool trusted = !outside[r] && spread[2 * r] < max_spread && spread[2 * r + 1] < max_spread;
+    const bool trusted = !outside[r] && spread[2 * r] < max_spread && spread[2 * r + 1] < max_spread &&
+                         (!local_test || local[r] < n->trust_max);
     used_fallback[r] = trusted ? 0 : 1;
     if (fallback_outcome) fallback_outcome[r] = LBM_RUN_SKIPPED;
     // the network is trained on (log U_t, log C_D)

@@ -79,7 +79,8 @@ EXPORTED = ["lbm_version", "lbm_required_bytes", "lbm_create", "lbm_init_bubbles
             "lbm_set_kernel_config", "lbm_batch_required_bytes", "lbm_batch_create", "lbm_batch_case",
             "lbm_batch_set_active", "lbm_batch_step", "lbm_batch_autotune", "lbm_batch_destroy",
             "lbm_batch_last_error", "lbm_batch_set_persistent", "lbm_batch_run", "surr_param_count", "surr_required_bytes", "surr_create", "surr_destroy",
-            "surr_last_error", "surr_get_weights", "surr_forward_backward", "surr_train", "surr_predict", "surr_answer"]
+            "surr_last_error", "surr_get_weights", "surr_forward_backward", "surr_train", "surr_predict", "surr_answer",
+            "surr_train_cv", "surr_local_residual", "surr_set_local_trust"]
 
 
 def load_library(path: str | None = None):
@@ -143,6 +144,10 @@ def load_library(path: str | None = None):
     lib.surr_train.argtypes = [vp, d, d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                ctypes.c_ulonglong, d]
     lib.surr_predict.argtypes = [vp, d, ctypes.c_int, d, d, P(ctypes.c_int)]
+    lib.surr_train_cv.argtypes = [vp, d, d, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_ulonglong, d, d]
+    lib.surr_local_residual.argtypes = [vp, d, ctypes.c_int, ctypes.c_int, d]
+    lib.surr_set_local_trust.argtypes = [vp, ctypes.c_int, ctypes.c_double]
     lib.surr_answer.argtypes = [vp, d, P(lbm_params), P(lbm_bubble), ctypes.c_int, ctypes.c_double,
                                 ctypes.c_double, P(lbm_run_opts), vp, ctypes.c_size_t, d, P(ctypes.c_int),
                                 P(ctypes.c_int)]
@@ -526,6 +531,29 @@ def surr_train(n, X, Y, epochs, batch, lr, seed=0) -> float:
     return float(fl[0])
 
 
+def surr_train_cv(n, X, Y, folds, epochs, batch, lr, seed, init_weights) -> float:
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    w = np.ascontiguousarray(init_weights, dtype=np.float64)
+    fl = np.zeros(1)
+    rc = load_library().surr_train_cv(n, _dptr(X), _dptr(Y), X.shape[0], int(folds), int(epochs), int(batch),
+                                      float(lr), int(seed), _dptr(w), _dptr(fl))
+    _check_surr(n, rc, "surr_train_cv")
+    return float(fl[0])
+
+
+def surr_local_residual(n, X, k) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    out = np.zeros(X.shape[0])
+    _check_surr(n, load_library().surr_local_residual(n, _dptr(X), X.shape[0], int(k), _dptr(out)),
+                "surr_local_residual")
+    return out
+
+
+def surr_set_local_trust(n, k, max_residual):
+    _check_surr(n, load_library().surr_set_local_trust(n, int(k), float(max_residual)), "surr_set_local_trust")
+
+
 def surr_predict(n, X):
     X = np.ascontiguousarray(X, dtype=np.float64)
     rows = X.shape[0]
@@ -585,8 +613,17 @@ class Surrogate:
     def train(self, X, Y, epochs, batch, lr, seed=0):
         return surr_train(self.n, X, Y, epochs, batch, lr, seed)
 
+    def train_cv(self, X, Y, folds, epochs, batch, lr, seed, init_weights):
+        return surr_train_cv(self.n, X, Y, folds, epochs, batch, lr, seed, init_weights)
+
     def predict(self, X):
         return surr_predict(self.n, X)
+
+    def local_residual(self, X, k):
+        return surr_local_residual(self.n, X, k)
+
+    def set_local_trust(self, k, max_residual):
+        surr_set_local_trust(self.n, k, max_residual)
 
     def answer(self, X, cases, bubbles, max_spread=0.05, noise_amp=1e-8, window=2000, rtol=0.05, max_steps=40000,
                top_margin=1.5):

@@ -4,8 +4,9 @@ The network (CUDA kernels behind ``surr_*`` in include/lbm.h) maps
 (n, Eo, log10 Mo, density ratio, log10 viscosity ratio) to (log U_t, log C_D).  Its
 training data are terminal states computed by the batched lattice Boltzmann
 solver (``lbm_batch_*``); its answer is used only when the input lies inside
-the box of the training inputs and the ensemble agrees within ``max_spread``;
-otherwise the case is solved directly.  This module only orchestrates: every
+the box of the training inputs, the ensemble agrees within ``max_spread`` and
+the training cases nearest to the input were predicted within ``local_max``
+when held out (cross validation); otherwise the case is solved directly.  This module only orchestrates: every
 time step and every network evaluation runs in the CUDA library.
 
 Terminal state (reading of Sec. 4.2-4.3, which gives no criterion): the rise
@@ -58,23 +59,48 @@ def run_to_terminal(cases, window=2000, rtol=0.05, max_steps=40000, stream=None,
 
 
 class TerminalStateModel:
-    """Ensemble surrogate with hull and agreement checks and solver fallback."""
+    """Ensemble surrogate with hull, agreement and local-residual checks and
+    solver fallback.
 
-    def __init__(self, members=5, seed=0, max_rows=4096, max_batch=512, max_spread=0.05):
-        self.net = lbm.Surrogate(inputs.mlp_init(members, seed=seed), max_batch=max_batch, max_rows=max_rows)
+    Local residual: the ensemble is also trained with `folds`-fold cross
+    validation on its own training set (surr_train_cv), and a case is trusted
+    only where the `local_k` training cases nearest to it were all predicted
+    within `local_max` (in log U_t and log C_D) when held out.  The labels are
+    terminal states under a stopping rule, and near some inputs they scatter
+    by more than the network's error; the members then agree with each other
+    and only held-out residuals reveal it."""
+
+    def __init__(self, members=5, seed=0, max_rows=4096, max_batch=512, max_spread=0.05, local_k=8,
+                 local_max=0.03):
+        self.init = inputs.mlp_init(members, seed=seed)
+        self.net = lbm.Surrogate(self.init, max_batch=max_batch, max_rows=max_rows)
         self.max_spread = max_spread
+        self.local_k, self.local_max = local_k, local_max
+        self.cv = False
 
-    def fit(self, X, U_t, C_D, epochs=400, batch=128, lr=2e-3, seed=0):
+    def fit(self, X, U_t, C_D, epochs=400, batch=128, lr=2e-3, seed=0, folds=5):
         Y = np.stack([np.log(U_t), np.log(C_D)], axis=1)
-        return self.net.train(np.asarray(X, dtype=np.float64), Y, epochs=epochs, batch=batch, lr=lr, seed=seed)
+        X = np.asarray(X, dtype=np.float64)
+        self.cv = folds > 1
+        if self.cv:
+            loss = self.net.train_cv(X, Y, folds, epochs, batch, lr, seed, self.init)
+        else:
+            loss = self.net.train(X, Y, epochs=epochs, batch=batch, lr=lr, seed=seed)
+        self.net.set_local_trust(self.local_k, self.local_max if self.cv else 0.0)
+        return loss
 
-    def predict(self, X):
-        """(U_t, C_D, trusted) per row: trusted means inside the training box
-        and no member farther than max_spread from the ensemble mean in either
-        output (relative: the outputs are logarithms)."""
-        mean, spread, outside = self.net.predict(np.asarray(X, dtype=np.float64))
+    def predict(self, X, local=True):
+        """(U_t, C_D, trusted) per row: trusted means inside the training box,
+        no member farther than max_spread from the ensemble mean in either
+        output (relative: the outputs are logarithms) and, after a
+        cross-validated fit (unless local=False), a local residual below
+        local_max."""
+        X = np.asarray(X, dtype=np.float64)
+        mean, spread, outside = self.net.predict(X)
         U, CD = np.exp(mean[:, 0]), np.exp(mean[:, 1])
         trusted = (~outside) & (spread[:, 0] < self.max_spread) & (spread[:, 1] < self.max_spread)
+        if local and self.cv and self.local_max > 0:
+            trusted &= self.net.local_residual(X, self.local_k) < self.local_max
         return U, CD, trusted
 
     def answer(self, cases, max_steps=40000, window=2000, rtol=0.05, stream=None):
@@ -110,11 +136,14 @@ def evaluate(n_train=1024, n_test=128, grid=(100, 200), members=5, epochs=1000, 
     t0 = time.perf_counter()
     Up, CDp, trusted = model.predict(Xt)
     wall_net = time.perf_counter() - t0
+    _, _, trusted_spread = model.predict(Xt, local=False)
     ok = np.array([r["finite"] and r["converged"] and r["U_t"] > 0 for r in ref])
     judged = trusted & ok
     cd_ref = np.array([r["C_D"] for r in ref])
     err = np.abs(CDp[judged] / cd_ref[judged] - 1.0)
     err_all = np.abs(CDp[ok] / cd_ref[ok] - 1.0)
+    js = trusted_spread & ok
+    err_spread = np.abs(CDp[js] / cd_ref[js] - 1.0)
     summary = {
         "train_cases": n_train, "train_converged": len(keep), "train_solver_s": round(wall_train, 2),
         "final_loss": loss, "test_cases": n_test, "test_converged": int(ok.sum()),
@@ -122,6 +151,12 @@ def evaluate(n_train=1024, n_test=128, grid=(100, 200), members=5, epochs=1000, 
         "cd_rel_err_median": float(np.median(err)) if err.size else None,
         "cd_rel_err_p90": float(np.percentile(err, 90)) if err.size else None,
         "cd_within_5pct": float(np.mean(err < 0.05)) if err.size else None,
+        "cd_rel_err_max": float(np.max(err)) if err.size else None,
+        "trust_rule": f"inside the training box, members within {max_spread:g} of the mean, the "
+                      f"{model.local_k} nearest training cases predicted within {model.local_max:g} out of fold",
+        "trusted_spread_only": int(trusted_spread.sum()), "judged_spread_only": int(js.sum()),
+        "cd_within_5pct_spread_only": float(np.mean(err_spread < 0.05)) if err_spread.size else None,
+        "cd_rel_err_max_spread_only": float(np.max(err_spread)) if err_spread.size else None,
         "cd_rel_err_median_all_converged": float(np.median(err_all)) if err_all.size else None,
         "cd_rel_err_p90_all_converged": float(np.percentile(err_all, 90)) if err_all.size else None,
         "solver_s_for_test": round(wall_solver, 3), "network_s_for_test": round(wall_net, 5),

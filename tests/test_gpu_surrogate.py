@@ -84,3 +84,36 @@ def test_training_fits_a_smooth_map_and_flags_outside_box(lbm):
     assert not outside.any() and spread.shape == (64, 2)
     _, _, out2 = net.predict(np.array([[0.0, 0.0, 0.0, 0.0, 1.5], [0.1, 0.1, 0.1, 0.1, 0.1]]))
     assert out2.tolist() == [True, False]
+
+
+def test_local_residual_finds_scattered_labels(lbm):
+    """Cross-validated training (surr_train_cv) on a smooth map whose labels
+    scatter by 20 % (in the logarithm) where x_0 > 0.5: the local residual is
+    large there and small elsewhere, although the ensemble's members agree on
+    both sides; k = 1 at a training input is that row's own out-of-fold
+    residual, and the residual grows with k."""
+    rng = np.random.default_rng(7)
+    X = rng.uniform(-1, 1, size=(400, 5))
+    Y = np.stack([np.sin(X[:, 0]) + 0.5 * X[:, 1], np.cos(X[:, 2]) - 0.3 * X[:, 3]], axis=1)
+    noisy = X[:, 0] > 0.5
+    Y[noisy] += rng.normal(scale=0.2, size=(int(noisy.sum()), 2))
+    w = inputs.mlp_init(3, seed=6)
+    net = lbm.Surrogate(w, max_batch=128, max_rows=400)
+    with pytest.raises(lbm.LbmError):
+        net.local_residual(X[:2], 3)          # before the cross-validated fit
+    net.train_cv(X, Y, 4, 300, 128, 3e-3, 2, w)
+    Xq = rng.uniform(-0.9, 0.9, size=(128, 5))
+    loc = net.local_residual(Xq, 5)
+    hi, lo = Xq[:, 0] > 0.6, Xq[:, 0] < 0.3
+    assert np.median(loc[hi]) > 3.0 * np.median(loc[lo])
+    _, spread, _ = net.predict(Xq)
+    assert np.median(spread[hi].max(1)) < np.median(loc[hi])   # the members do not see the scatter
+    own = net.local_residual(X, 1)
+    assert np.all(own >= 0) and np.all(np.isfinite(own))
+    assert np.median(own[noisy]) > 3.0 * np.median(own[~noisy])
+    assert np.all(net.local_residual(Xq, 9) >= loc)
+    assert np.allclose(net.local_residual(Xq[:3], 400), own.max())
+    # a plain fit forgets the residuals of the earlier set
+    net.train(X, Y, epochs=1, batch=128, lr=1e-3, seed=0)
+    with pytest.raises(lbm.LbmError):
+        net.local_residual(X[:2], 3)
