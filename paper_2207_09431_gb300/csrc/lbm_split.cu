@@ -45,9 +45,11 @@ __device__ __forceinline__ long long shifted(const DevParams &P, int x, int y, i
 
 // Directional derivative e_a . grad X from samples X(x - e), X(x), X(x + e),
 // X(x + 2e) (R2; mixed = mean of central and second-order biased forms).
+// The final scaling is a separate rounding (__fmul_rn), never fused into the
+// caller's next addition, whether or not this is inlined.
 __device__ __forceinline__ float dir_deriv(int scheme, float xm, float x0, float xp, float xpp) {
-  if (scheme == 0) return 0.5f * (xp - xm);
-  return 0.25f * (-xpp + 5.0f * xp - 3.0f * x0 - xm);
+  if (scheme == 0) return __fmul_rn(0.5f, xp - xm);
+  return __fmul_rn(0.25f, -xpp + 5.0f * xp - 3.0f * x0 - xm);
 }
 
 // Everything the forcing terms need at one node.
@@ -58,7 +60,8 @@ struct NodeCtx {
 };
 
 // Gathers C (radius 1 or 2), rho (from C), p (radius 1 or 2) around (x, y).
-__device__ void gather_gradients(const DevParams &P, const CReader &cr, const float *pf, int x, int y,
+// Inlined, so that NodeCtx stays in registers.
+__device__ __forceinline__ void gather_gradients(const DevParams &P, const CReader &cr, const float *pf, int x, int y,
                                  NodeCtx &n) {
   const long long k0 = node_index(P, x, y);
   float Cn[9][3], rn[9], pn[9];
@@ -151,10 +154,11 @@ __global__ void k_moments(DevParams P, const float *__restrict__ h, float *__res
 // (Eq. 5, 22-24): C and rho at the node and its neighbours, grad C, lap C,
 // grad rho, mu_1..3, the forces, the moments of g and u.  Shared by k_fields
 // and the observables, so that both see the same velocity.
+template <int NH>
 __device__ __forceinline__ void fields_core(const DevParams &P, const float *__restrict__ Cf,
                                             const float *__restrict__ g, int x, int y, long long k, NodeCtx &n,
                                             float (&Cn)[9][3], float (&rn)[9], float (&ga)[9], float &m0) {
-  CReader cr{Cf, P.plane, P.nh};
+  CReader cr{Cf, P.plane, NH};
   for (int a = 0; a < 9; ++a) {
     long long kk = shifted(P, x, y, ex(a), ey(a));
     cr.at(kk, Cn[a]);
@@ -201,6 +205,7 @@ __device__ __forceinline__ void fields_core(const DevParams &P, const float *__r
 }
 
 // rho, mu_1..3, u, p and (if write_tau) the new relaxation time and strain rate.
+template <int NH>
 __global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float *__restrict__ g,
                          const float *__restrict__ tau_prev, float *__restrict__ mu, float *__restrict__ pf,
                          float *__restrict__ uxf, float *__restrict__ uyf, float *__restrict__ tau_new,
@@ -208,10 +213,10 @@ __global__ void k_fields(DevParams P, const float *__restrict__ Cf, const float 
   int x, y;
   if (!node_of_thread(P, x, y)) return;
   const long long k = node_index(P, x, y);
-  CReader cr{Cf, P.plane, P.nh};
+  CReader cr{Cf, P.plane, NH};
   float Cn[9][3], rn[9], ga[9], m0;
   NodeCtx n;
-  fields_core(P, Cf, g, x, y, k, n, Cn, rn, ga, m0);
+  fields_core<NH>(P, Cf, g, x, y, k, n, Cn, rn, ga, m0);
   n.p = m0 + 0.5f * kCs2 * (n.ux * n.grho[0] + n.uy * n.grho[1]);
   for (int j = 0; j < 3; ++j) mu[(long long)j * P.plane + k] = n.mu[j];
   pf[k] = n.p;
@@ -293,6 +298,7 @@ __global__ void k_sources(DevParams P, const float *__restrict__ Cf, const float
 // x + e_a; populations that would cross a wall return to x in the opposite
 // direction.  With tau_h = 1/2 the BGK step of Eq. 18 replaces h by its
 // modified equilibrium, so h itself is not read: h* = C Gamma + Phi/2 + SV Gamma/2.
+template <int NH>
 __global__ void k_collide(DevParams P, const float *__restrict__ g, const float *__restrict__ Cf,
                           const float *__restrict__ mu, const float *__restrict__ pf, const float *__restrict__ uxf,
                           const float *__restrict__ uyf, const float *__restrict__ tau_new,
@@ -300,7 +306,7 @@ __global__ void k_collide(DevParams P, const float *__restrict__ g, const float 
   int x, y;
   if (!node_of_thread(P, x, y)) return;
   const long long k = node_index(P, x, y);
-  CReader cr{Cf, P.plane, P.nh};
+  CReader cr{Cf, P.plane, NH};
   NodeCtx n;
   gather_gradients(P, cr, pf, x, y, n);
   n.ux = uxf[k];
@@ -312,7 +318,10 @@ __global__ void k_collide(DevParams P, const float *__restrict__ g, const float 
   n.Fb[1] = -n.rho * P.gravity;
   const float omega = 1.0f / (tau_new[k] + 0.5f);
   float sv[2] = {0.f, 0.f};
-  for (int i = 0; i < P.nh; ++i) sv[i] = SV[(long long)i * P.plane + k];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+    if (i < NH) sv[i] = SV[(long long)i * P.plane + k];
+#pragma unroll
   for (int a = 0; a < 9; ++a) {
     const float G = gamma_a(a, n.ux, n.uy);
     const float pg = phi_g(n, a, G);
@@ -333,10 +342,12 @@ __global__ void k_collide(DevParams P, const float *__restrict__ g, const float 
     }
     g_out[pop_index(kd, da, 9)] = gstar;
     const float Gd = gamma_a(da, uxf[kd], uyf[kd]);
-    for (int i = 0; i < P.nh; ++i) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      if (i >= NH) break;
       const float ph = phi_h(n, i, a, G);
       const float hstar = n.C[i] * G + 0.5f * ph + 0.5f * sv[i] * G;
-      h_out[pop_index(kd, i * 9 + da, 9 * P.nh)] = hstar + 0.5f * SV[(long long)i * P.plane + kd] * Gd;
+      h_out[pop_index(kd, i * 9 + da, 9 * NH)] = hstar + 0.5f * SV[(long long)i * P.plane + kd] * Gd;
     }
   }
 }
@@ -412,13 +423,14 @@ __global__ void k_open_x(DevParams P, const float *__restrict__ g_old, const flo
 
 // Modified equilibria (Eq. 16, 20) of given C, p, u, and tau at zero strain
 // rate (reading R11).  C, p, u are in the scratch planes.
+template <int NH>
 __global__ void k_init(DevParams P, const float *__restrict__ Cf, const float *__restrict__ pf,
                        const float *__restrict__ uxf, const float *__restrict__ uyf, float *__restrict__ g,
                        float *__restrict__ h, float *__restrict__ tau) {
   int x, y;
   if (!node_of_thread(P, x, y)) return;
   const long long k = node_index(P, x, y);
-  CReader cr{Cf, P.plane, P.nh};
+  CReader cr{Cf, P.plane, NH};
   NodeCtx n;
   gather_gradients(P, cr, pf, x, y, n);
   float Cn[9][3], lapC[3];
@@ -438,9 +450,11 @@ __global__ void k_init(DevParams P, const float *__restrict__ Cf, const float *_
   for (int a = 0; a < 9; ++a) {
     const float G = gamma_a(a, n.ux, n.uy);
     g[pop_index(k, a, 9)] = wt(a) * n.p + n.rho * kCs2 * (G - wt(a)) - 0.5f * phi_g(n, a, G);
-    if (h)
-      for (int i = 0; i < P.nh; ++i)
-        h[pop_index(k, i * 9 + a, 9 * P.nh)] = n.C[i] * G - 0.5f * phi_h(n, i, a, G);
+    if (h) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+        if (i < NH) h[pop_index(k, i * 9 + a, 9 * NH)] = n.C[i] * G - 0.5f * phi_h(n, i, a, G);
+    }
   }
   const float tau1 = P.powerlaw ? tau_powerlaw(P, 0.0f, 1.0f / n.rho) : P.tau[0];
   tau[k] = tau_mix(P, n.C[0], n.C[1], n.C[2], tau1);
@@ -465,32 +479,71 @@ __global__ void k_planes_from_f64(DevParams P, const double *__restrict__ src, f
         x < P.nx ? (float)src[((long long)q * P.ny + y) * P.nx + x] : 0.0f;
 }
 
+// A running FP32 sum with Neumaier's compensation: c collects the rounding
+// error of every addition (and, in add_prod, the exact error of the product,
+// from fmaf), so s + c, taken in FP64, is the exact sum of a short run of
+// terms up to a relative error of order n 2^-48.  Explicit _rn intrinsics keep
+// the compiler from fusing a product into the next addition.
+struct CompSum {
+  float s, c;
+  __device__ __forceinline__ void add(float v) {
+    const float t = __fadd_rn(s, v);
+    c = __fadd_rn(c, fabsf(s) >= fabsf(v) ? __fadd_rn(__fsub_rn(s, t), v) : __fadd_rn(__fsub_rn(v, t), s));
+    s = t;
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    add(p);
+    c = __fadd_rn(c, __fmaf_rn(a, b, -p));
+  }
+};
+
+// Nodes a thread sums in FP32 (compensated) before it adds the run to its
+// FP64 totals: GB300's FP64 pipe runs at a small fraction of its FP32 rate, so
+// one FP64 addition per node and quantity bound the kernel.
+constexpr int kObsRun = 16;
+
 // The observable sums straight from the state: C from the C planes, u
 // computed at each node as k_fields computes it (fields_core), without
 // writing the macro fields.
+template <int NH>
 __global__ void __launch_bounds__(kObsThreads) k_obs_direct(DevParams P, const float *__restrict__ Cf,
                                                             const float *__restrict__ g, int gas_comp,
                                                             double *acc, int *ext) {
   double v[11];
-  for (int q = 0; q < 11; ++q) v[q] = 0.0;
+  CompSum r[11];
+  for (int q = 0; q < 11; ++q) {
+    v[q] = 0.0;
+    r[q] = {0.f, 0.f};
+  }
+  int run = 0;
+  auto flush = [&]() {
+    for (int q = 0; q < 11; ++q) {
+      v[q] += (double)r[q].s + (double)r[q].c;
+      r[q] = {0.f, 0.f};
+    }
+    run = 0;
+  };
   int e[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
   for (int y = blockIdx.x; y < P.ny; y += gridDim.x) {
     for (int x = threadIdx.x; x < P.nx; x += blockDim.x) {
       const long long k = node_index(P, x, y);
       NodeCtx n;
       float Cn[9][3], rn[9], ga[9], m0;
-      fields_core(P, Cf, g, x, y, k, n, Cn, rn, ga, m0);
+      fields_core<NH>(P, Cf, g, x, y, k, n, Cn, rn, ga, m0);
       for (int i = 0; i < 3; ++i) {
-        v[i] += n.C[i];
-        v[3 + i] += n.C[i] > 0.5f ? (double)n.C[i] : 0.0;
+        r[i].add(n.C[i]);
+        r[3 + i].add(n.C[i] > 0.5f ? n.C[i] : 0.0f);
       }
-      const double cg = n.C[gas_comp - 1];
-      v[6] += cg;
-      v[7] += cg * x;
-      v[8] += cg * y;
-      v[9] += cg * n.ux;
-      v[10] += cg * n.uy;
-      if (n.C[gas_comp - 1] > 0.5f) {
+      // C of the gas component, selected without indexing (keeps n in registers)
+      const float cg = gas_comp == 1 ? n.C[0] : (gas_comp == 2 ? n.C[1] : n.C[2]);
+      r[6].add(cg);
+      r[7].add_prod(cg, (float)x);  // x, y < 2^24: exact in FP32
+      r[8].add_prod(cg, (float)y);
+      r[9].add_prod(cg, n.ux);
+      r[10].add_prod(cg, n.uy);
+      if (++run == kObsRun) flush();
+      if (cg > 0.5f) {
         e[0] = min(e[0], x);
         e[1] = min(e[1], -x);
         e[2] = min(e[2], y);
@@ -498,6 +551,7 @@ __global__ void __launch_bounds__(kObsThreads) k_obs_direct(DevParams P, const f
       }
     }
   }
+  flush();
   for (int off = 16; off > 0; off >>= 1) {
     for (int q = 0; q < 11; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
     for (int q = 0; q < 4; ++q) e[q] = min(e[q], __shfl_down_sync(0xffffffffu, e[q], off));
@@ -532,11 +586,17 @@ void launch_split_step(const DevParams &P, const StepBuffers &B, cudaStream_t s,
   if (ev) cudaEventRecord(ev[0], s);
   k_moments<<<grd, blk, 0, s>>>(P, B.h_in, B.C);
   if (ev) cudaEventRecord(ev[1], s);
-  k_fields<<<grd, blk, 0, s>>>(P, B.C, B.g_in, B.tau_in, B.mu, B.p, B.ux, B.uy, B.tau_out, B.shear, B.err, 1);
+  if (P.nh == 1)
+    k_fields<1><<<grd, blk, 0, s>>>(P, B.C, B.g_in, B.tau_in, B.mu, B.p, B.ux, B.uy, B.tau_out, B.shear, B.err, 1);
+  else
+    k_fields<2><<<grd, blk, 0, s>>>(P, B.C, B.g_in, B.tau_in, B.mu, B.p, B.ux, B.uy, B.tau_out, B.shear, B.err, 1);
   if (ev) cudaEventRecord(ev[2], s);
   k_sources<<<grd, blk, 0, s>>>(P, B.C, B.mu, B.SV);
   if (ev) cudaEventRecord(ev[3], s);
-  k_collide<<<grd, blk, 0, s>>>(P, B.g_in, B.C, B.mu, B.p, B.ux, B.uy, B.tau_out, B.SV, B.g_out, B.h_out);
+  if (P.nh == 1)
+    k_collide<1><<<grd, blk, 0, s>>>(P, B.g_in, B.C, B.mu, B.p, B.ux, B.uy, B.tau_out, B.SV, B.g_out, B.h_out);
+  else
+    k_collide<2><<<grd, blk, 0, s>>>(P, B.g_in, B.C, B.mu, B.p, B.ux, B.uy, B.tau_out, B.SV, B.g_out, B.h_out);
   if (P.open_x)
     k_open_x<<<(P.ny + 127) / 128, 128, 0, s>>>(P, B.g_in, B.h_in, B.C, B.p, B.ux, B.uy, B.SV, B.g_out, B.h_out);
   if (ev) cudaEventRecord(ev[4], s);
@@ -546,7 +606,10 @@ void launch_macros(const DevParams &P, const StepBuffers &B, cudaStream_t s) {
   const dim3 blk(32, 8);
   const dim3 grd = node_grid(P, blk);
   if (B.h_in) k_moments<<<grd, blk, 0, s>>>(P, B.h_in, B.C);  // null: the state holds C
-  k_fields<<<grd, blk, 0, s>>>(P, B.C, B.g_in, B.tau_in, B.mu, B.p, B.ux, B.uy, nullptr, nullptr, B.err, 0);
+  if (P.nh == 1)
+    k_fields<1><<<grd, blk, 0, s>>>(P, B.C, B.g_in, B.tau_in, B.mu, B.p, B.ux, B.uy, nullptr, nullptr, B.err, 0);
+  else
+    k_fields<2><<<grd, blk, 0, s>>>(P, B.C, B.g_in, B.tau_in, B.mu, B.p, B.ux, B.uy, nullptr, nullptr, B.err, 0);
 }
 
 cudaError_t launch_planes_from_f64(const DevParams &P, const double *src, float *dst, int nplanes, cudaStream_t s) {
@@ -556,7 +619,10 @@ cudaError_t launch_planes_from_f64(const DevParams &P, const double *src, float 
 
 void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s) {
   const dim3 blk(32, 8);
-  k_init<<<node_grid(P, blk), blk, 0, s>>>(P, B.C, B.p, B.ux, B.uy, B.g_out, B.h_out, B.tau_out);
+  if (P.nh == 1)
+    k_init<1><<<node_grid(P, blk), blk, 0, s>>>(P, B.C, B.p, B.ux, B.uy, B.g_out, B.h_out, B.tau_out);
+  else
+    k_init<2><<<node_grid(P, blk), blk, 0, s>>>(P, B.C, B.p, B.ux, B.uy, B.g_out, B.h_out, B.tau_out);
 }
 
 void launch_moments(const DevParams &P, const float *h, float *C, cudaStream_t s) {
@@ -567,7 +633,10 @@ void launch_moments(const DevParams &P, const float *h, float *C, cudaStream_t s
 void launch_observables_direct(const DevParams &P, const float *C, const float *g, int gas_comp, double *acc,
                                int *ext, cudaStream_t s) {
   const int blocks = P.ny < 1216 ? P.ny : 1216;  // 8 per SM on 152 SMs, at most one per row
-  k_obs_direct<<<blocks, kObsThreads, 0, s>>>(P, C, g, gas_comp, acc, ext);
+  if (P.nh == 1)
+    k_obs_direct<1><<<blocks, kObsThreads, 0, s>>>(P, C, g, gas_comp, acc, ext);
+  else
+    k_obs_direct<2><<<blocks, kObsThreads, 0, s>>>(P, C, g, gas_comp, acc, ext);
 }
 
 
