@@ -101,8 +101,8 @@ struct lbm_batch {
           for (int x0 = 0; x0 < h[i]->dp.nx; x0 += tx) w.push_back({i, x0, y0, y0 + ty < ny ? y0 + ty : ny});
       }
     }
-    // longest items first: the CTAs take items in order (one launch per step)
-    // or round robin (persistent launch), which then approximates the
+    // longest items first: the CTAs take items in order (one launch per step,
+    // or from a counter in the persistent launch), which then approximates the
     // longest-processing-time schedule
     std::stable_sort(w.begin(), w.end(), [](const lbm::WorkItem &a, const lbm::WorkItem &b) {
       return a.y1 - a.y0 > b.y1 - b.y0;

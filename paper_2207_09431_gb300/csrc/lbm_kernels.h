@@ -57,6 +57,8 @@ struct WorkItem {
 // ran out of its iteration limit).  Zeroed by the host before each launch.
 struct GridSync {
   unsigned count, gen, status, pad;
+  unsigned next[2];  // work-item counters of even and odd steps (dynamic assignment)
+  unsigned pad2[2];
 };
 constexpr unsigned kSyncTimeout = 1u;
 

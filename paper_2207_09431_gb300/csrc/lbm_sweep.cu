@@ -537,10 +537,14 @@ __device__ __forceinline__ bool grid_barrier(GridSync *gs, unsigned nblocks, lon
   return go_on != 0;
 }
 
-// The batched sweep as one persistent launch: CTA b takes work items b,
-// b + gridDim.x, ... of every time step, and all CTAs (resident at once: a
+// The batched sweep as one persistent launch: in every time step CTA b takes
+// work item b first and then, while items are left, the next one from the
+// step's counter (items longest first, so that this approximates the
+// longest-processing-time schedule online); all CTAs (resident at once: a
 // cooperative launch) meet at the grid barrier before the next step reads
-// what this one wrote.
+// what this one wrote.  Every CTA takes items until the counter runs past the
+// list, before it reaches the barrier, so a step's counter is idle from that
+// barrier on: block 0 clears it during the step after, for the step after that.
 template <int TX, int RS, int NH, int FORM, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_sweep_persistent(const BatchCase *__restrict__ cases,
                                                                const WorkItem *__restrict__ work, int nwork,
@@ -549,9 +553,11 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep_persistent(const BatchCase *
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevParams sP;
   __shared__ FusedBuffers sB;
+  __shared__ int s_next;
   for (int t = 0; t < nsteps; ++t) {
     const int parity = (parity0 + t) & 1;
-    for (int i = blockIdx.x; i < nwork; i += gridDim.x) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) sync->next[(t + 1) & 1] = 0u;  // last used in step t - 1
+    for (int i = blockIdx.x; i < nwork;) {
       const WorkItem w = work[i];
       if (threadIdx.x == 0) {
         sP = cases[w.case_id].P;
@@ -561,6 +567,9 @@ __global__ void __launch_bounds__(NT, MINB) k_sweep_persistent(const BatchCase *
       sweep_body<TX, RS, NH, FORM, 2, NT>(sP, sB, w.x0, w.y0, w.y1,
                                           *reinterpret_cast<PipeSmem<TX, RS, NH, FORM != 0> *>(smem_raw));
       __syncthreads();  // sP and sB are rewritten by the next item
+      if (threadIdx.x == 0) s_next = (int)gridDim.x + (int)atomicAdd(&sync->next[t & 1], 1u);
+      __syncthreads();
+      i = s_next;
     }
     if (t + 1 < nsteps && !grid_barrier(sync, gridDim.x, spin_limit)) return;
   }
