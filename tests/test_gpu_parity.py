@@ -206,6 +206,44 @@ def test_checkpoint_resume_bit_identical(lbm, tmp_path):
         assert np.array_equal(a.field(name), b.field(name))
 
 
+def test_damaged_checkpoints_are_refused_and_the_state_kept(lbm, tmp_path):
+    """Checkpoint faults made on the host: a truncated file and a foreign file
+    give LBM_E_IO, a checkpoint of other parameters LBM_E_INVAL, a missing
+    file LBM_E_IO; after each refusal the handle keeps its state and steps on
+    exactly as an untouched one."""
+    p, C = _bubble_case(40, 60)
+    a = lbm.Lattice(p)
+    a.set_fields(C)
+    a.step(10)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    raw = open(path, "rb").read()
+    bad = {"truncated": raw[: len(raw) // 2], "foreign": b"NOTACKPT" + raw[8:]}
+    b = lbm.Lattice(p)
+    b.set_fields(C)
+    b.step(10)
+    before = {n: b.field(n) for n in ("g", "h", "tau")}
+    for name, data in bad.items():
+        q = str(tmp_path / (name + ".bin"))
+        open(q, "wb").write(data)
+        with pytest.raises(lbm.LbmError) as ei:
+            b.load(q)
+        assert ei.value.status == -7, name
+    with pytest.raises(lbm.LbmError) as ei:
+        b.load(str(tmp_path / "missing.bin"))
+    assert ei.value.status == -7
+    other = lbm.Lattice(dict(p, gravity=2.0 * p["gravity"]))
+    with pytest.raises(lbm.LbmError) as ei:
+        other.load(path)
+    assert ei.value.status == -1
+    for n, v in before.items():
+        assert np.array_equal(b.field(n), v), n
+    a.step(5)
+    b.step(5)
+    for n in ("g", "h", "tau"):
+        assert np.array_equal(a.field(n), b.field(n)), n
+
+
 def test_divergence_is_reported(lbm):
     """A non-finite state is caught by the watchdog (injected on the host)."""
     p, C = _bubble_case(32, 48)
