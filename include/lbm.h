@@ -343,7 +343,9 @@ lbm_status surr_train(surr_net *n, const double *X, const double *Y, int rows, i
  * |prediction - target| over the two outputs (relative errors, as the outputs
  * are logarithms).  Then the ensemble is trained on every row as surr_train
  * does (final_loss as there).  The rows and residuals are kept (host memory)
- * for surr_local_residual.  Costs folds + 1 trainings. */
+ * for surr_local_residual.  Costs folds + 1 trainings.  On an error after the
+ * arguments were accepted the ensemble is left untrained (surr_predict then
+ * returns LBM_E_STATE). */
 lbm_status surr_train_cv(surr_net *n, const double *X, const double *Y, int rows, int folds, int epochs, int batch,
                          double lr, unsigned long long seed, const double *init_weights, double *final_loss);
 /* For each of rows x 5 raw inputs, the largest out-of-fold residual among the

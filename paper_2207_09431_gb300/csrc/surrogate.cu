@@ -465,10 +465,25 @@ static lbm_status surr_reset(surr_net *n, const double *init_weights) {
   return LBM_OK;
 }
 
+static lbm_status train_cv(surr_net *n, const double *X, const double *Y, int rows, int folds, int epochs, int batch,
+                           double lr, unsigned long long seed, const double *init_weights, double *final_loss);
+
 lbm_status surr_train_cv(surr_net *n, const double *X, const double *Y, int rows, int folds, int epochs, int batch,
                          double lr, unsigned long long seed, const double *init_weights, double *final_loss) {
   if (!n || !X || !Y || !init_weights || rows < folds || folds < 2 || folds > 16 || rows > n->max_rows)
     return LBM_E_INVAL;
+  const lbm_status s = train_cv(n, X, Y, rows, folds, epochs, batch, lr, seed, init_weights, final_loss);
+  if (s != LBM_OK) {
+    // the weights are those of an interrupted fold: not a usable ensemble
+    n->trained = false;
+    n->cv_x.clear();
+    n->cv_res.clear();
+  }
+  return s;
+}
+
+static lbm_status train_cv(surr_net *n, const double *X, const double *Y, int rows, int folds, int epochs, int batch,
+                           double lr, unsigned long long seed, const double *init_weights, double *final_loss) {
   // fold of each row: position in a seeded permutation, modulo folds
   std::vector<int> perm(rows), fold(rows);
   for (int r = 0; r < rows; ++r) perm[r] = r;
