@@ -35,7 +35,7 @@ METRIC = "coupled-step MLUPS (D2Q9, 2 components, FP32)"
 UNIT = "MLUPS"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
@@ -55,7 +55,9 @@ def parse():
                     help="launch configuration of the step kernel (default: autotuned)")
     ap.add_argument("--stability", action="store_true",
                     help="also compare the central and mixed difference schemes on the 36-case paper grid")
-    return ap.parse_args()
+    ap.add_argument("--reference-seconds", type=float, default=150.0,
+                    help="host time the reference arm spends in its warm-up and timed steps together")
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -680,11 +682,11 @@ def run_reference(args):
     o = oracle.Oracle(p, "f64-omp")
     o.set_fields(C)
     # lattice steps per bench step: a bounded sample, sized so that the whole
-    # run (warm-up and timed steps) takes about 150 s of host time
+    # run (warm-up and timed steps) takes about --reference-seconds of host time
     t0 = time.perf_counter()
     o.step(1)
     t_one = time.perf_counter() - t0
-    sub = max(1, int(150.0 / (max(args.steps + args.warmup, 1) * max(t_one, 1e-6))))
+    sub = max(1, int(args.reference_seconds / (max(args.steps + args.warmup, 1) * max(t_one, 1e-6))))
     o.step(args.warmup * sub)
     t0 = time.perf_counter()
     o.step(args.steps * sub)
