@@ -3,6 +3,7 @@
 // readback, observables post-processing (Sec. 4.1-4.2) and checkpoints.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -125,11 +126,71 @@ lbm_status lbm_create(const lbm_params *p, void *dev_arena, size_t arena_bytes, 
   return LBM_OK;
 }
 
+// Whether lbm_set_fields may overlap the upload of C with the conversion and
+// the initial equilibria: FP32 populations (the FP16 form computes its
+// equilibria into the staging buffer), chunks of at least 16 rows (the
+// equilibria read two rows beyond their own), and a stream that is not being
+// captured.  The copy stream and its events are created on first use.
+static bool upload_overlappable(lbm_handle *h) {
+  if (h->dp.g16 || h->prm.ny < 16 * lbm_handle::kUploadChunks) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+  if (!h->copy_stream && cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    h->copy_stream = nullptr;
+    return false;
+  }
+  for (auto &ev : h->upload_ev)
+    if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      ev = nullptr;
+      return false;
+    }
+  return true;
+}
+
+// C goes up in row chunks on the copy stream; the handle's stream converts each
+// chunk once it has arrived and computes the equilibria of the rows whose
+// two-row neighbourhood is converted (those of the first chunk last under
+// periodic y, where they read the last rows).  Same node values as one upload.
+static cudaError_t upload_and_init_overlapped(lbm_handle *h, const double *C, int nh, const lbm::StepBuffers &B) {
+  constexpr int n = lbm_handle::kUploadChunks;
+  const int nx = h->prm.nx, ny = h->prm.ny, rows = (ny + n - 1) / n;
+  const bool per = h->prm.periodic_y != 0;
+  double *staging = reinterpret_cast<double *>(h->g[1]);
+  // the staging buffer is free once the uploads before on the stream are done
+  cudaError_t e = cudaEventRecord(h->upload_ev[n], h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->upload_ev[n], 0);
+  for (int c = 0; c < n && e == cudaSuccess; ++c) {
+    const int y0 = c * rows, y1 = std::min(ny, y0 + rows);
+    for (int q = 0; q < nh && e == cudaSuccess; ++q) {
+      const size_t off = ((size_t)q * ny + y0) * nx;
+      e = cudaMemcpyAsync(staging + off, C + off, (size_t)(y1 - y0) * nx * sizeof(double), cudaMemcpyHostToDevice,
+                          h->copy_stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(h->upload_ev[c], h->copy_stream);
+  }
+  for (int c = 0; c < n && e == cudaSuccess; ++c) {
+    const int y0 = c * rows, y1 = std::min(ny, y0 + rows);
+    e = cudaStreamWaitEvent(h->stream, h->upload_ev[c], 0);
+    if (e == cudaSuccess) e = lbm::launch_planes_from_f64_rows(h->dp, staging, h->C, nh, y0, y1, h->stream);
+    if (e == cudaSuccess && c >= 1 && (c >= 2 || !per)) {
+      lbm::launch_init_rows(h->dp, B, (c - 1) * rows, c * rows, h->stream);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) {
+    lbm::launch_init_rows(h->dp, B, (n - 1) * rows, ny, h->stream);
+    if (per) lbm::launch_init_rows(h->dp, B, 0, rows, h->stream);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
 lbm_status lbm_set_fields(lbm_handle *h, const double *C, const double *p, const double *ux, const double *uy) {
   if (!h) return LBM_E_INVAL;
   if (!C) return h->fail(LBM_E_INVAL, "C is NULL");
   const int nh = h->prm.ncomp - 1;
-  cudaError_t e = upload_planes(h, h->C, C, nh);
+  const bool overlap = upload_overlappable(h);
+  cudaError_t e = overlap ? cudaSuccess : upload_planes(h, h->C, C, nh);
   if (e == cudaSuccess) e = upload_planes(h, h->p, p, 1);
   if (e == cudaSuccess) e = upload_planes(h, h->ux, ux, 1);
   if (e == cudaSuccess) e = upload_planes(h, h->uy, uy, 1);
@@ -140,11 +201,16 @@ lbm_status lbm_set_fields(lbm_handle *h, const double *C, const double *p, const
   if (h->prm.collapse_h) {
     B.C = h->C;
     B.h_out = nullptr;
-    e = cudaMemcpyAsync(h->h[0], h->C, (size_t)nh * h->L.plane_bytes, cudaMemcpyDeviceToDevice, h->stream);
-    if (e != cudaSuccess) return h->cuda_fail(e, "lbm_set_fields copy");
   }
-  lbm::launch_init(h->dp, B, h->stream);
-  e = cudaGetLastError();
+  if (overlap) {
+    e = upload_and_init_overlapped(h, C, nh, B);
+  } else {
+    lbm::launch_init(h->dp, B, h->stream);
+    e = cudaGetLastError();
+  }
+  // the C state: the converted order parameters
+  if (e == cudaSuccess && h->prm.collapse_h)
+    e = cudaMemcpyAsync(h->h[0], h->C, (size_t)nh * h->L.plane_bytes, cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess && h->dp.g16) e = lbm::launch_g16_encode(h->dp, h->g[1], h->g[0], h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return h->cuda_fail(e, "lbm_set_fields init kernel");

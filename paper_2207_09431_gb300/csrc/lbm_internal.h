@@ -23,6 +23,12 @@ void launch_moments(const DevParams &P, const float *h, float *C, cudaStream_t s
 // accumulated with atomics.
 void launch_observables_direct(const DevParams &P, const float *C, const float *g, int gas_comp, double *acc,
                                int *ext, cudaStream_t s);
+// Rows [y0, y1) of nplanes dense FP64 planes into pitched FP32 planes.
+cudaError_t launch_planes_from_f64_rows(const DevParams &P, const double *src, float *dst, int nplanes, int y0,
+                                        int y1, cudaStream_t s);
+// Initial equilibria (modified, Eq. 14 and 18 at rest of the forcing) of rows
+// [y0, y1); they read C and p up to two rows beyond.
+void launch_init_rows(const DevParams &P, const StepBuffers &B, int y0, int y1, cudaStream_t s);
 }  // namespace lbm
 
 namespace lbm_detail {
@@ -199,10 +205,18 @@ struct lbm_handle {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_variant[2] = {-1, -1};
   static constexpr int kStepGraph = 16;
+  // lbm_set_fields: a stream of its own for the upload of C in row chunks,
+  // overlapped with the conversion and initial equilibria on `stream`
+  static constexpr int kUploadChunks = 4;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t upload_ev[kUploadChunks + 1] = {};
 
   ~lbm_handle() {
     for (auto &g : graph)
       if (g) cudaGraphExecDestroy(g);
+    for (auto &e : upload_ev)
+      if (e) cudaEventDestroy(e);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
   }
 
   lbm_status fail(lbm_status s, const std::string &msg) {

@@ -426,9 +426,9 @@ __global__ void k_open_x(DevParams P, const float *__restrict__ g_old, const flo
 template <int NH>
 __global__ void k_init(DevParams P, const float *__restrict__ Cf, const float *__restrict__ pf,
                        const float *__restrict__ uxf, const float *__restrict__ uyf, float *__restrict__ g,
-                       float *__restrict__ h, float *__restrict__ tau) {
-  int x, y;
-  if (!node_of_thread(P, x, y)) return;
+                       float *__restrict__ h, float *__restrict__ tau, int y0, int y1) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = y0 + blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= P.nx || y >= y1) return;
   const long long k = node_index(P, x, y);
   CReader cr{Cf, P.plane, NH};
   NodeCtx n;
@@ -471,8 +471,8 @@ constexpr int kObsThreads = 256;
 // thread per column of the pitch (the padding columns get 0); FP64 -> FP32
 // rounds to nearest, as a host conversion does.
 __global__ void k_planes_from_f64(DevParams P, const double *__restrict__ src, float *__restrict__ dst,
-                                  int nplanes) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+                                  int nplanes, int y0) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = y0 + blockIdx.y;
   if (x >= P.pitch) return;
   for (int q = 0; q < nplanes; ++q)
     dst[(long long)q * P.plane + (long long)y * P.pitch + x] =
@@ -612,18 +612,30 @@ void launch_macros(const DevParams &P, const StepBuffers &B, cudaStream_t s) {
     k_fields<2><<<grd, blk, 0, s>>>(P, B.C, B.g_in, B.tau_in, B.mu, B.p, B.ux, B.uy, nullptr, nullptr, B.err, 0);
 }
 
-cudaError_t launch_planes_from_f64(const DevParams &P, const double *src, float *dst, int nplanes, cudaStream_t s) {
-  k_planes_from_f64<<<dim3((P.pitch + 127) / 128, P.ny), 128, 0, s>>>(P, src, dst, nplanes);
+// Rows [y0, y1) of nplanes dense FP64 planes into the pitched FP32 planes.
+cudaError_t launch_planes_from_f64_rows(const DevParams &P, const double *src, float *dst, int nplanes, int y0,
+                                        int y1, cudaStream_t s) {
+  if (y1 <= y0) return cudaSuccess;
+  k_planes_from_f64<<<dim3((P.pitch + 127) / 128, y1 - y0), 128, 0, s>>>(P, src, dst, nplanes, y0);
   return cudaGetLastError();
 }
 
-void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s) {
-  const dim3 blk(32, 8);
-  if (P.nh == 1)
-    k_init<1><<<node_grid(P, blk), blk, 0, s>>>(P, B.C, B.p, B.ux, B.uy, B.g_out, B.h_out, B.tau_out);
-  else
-    k_init<2><<<node_grid(P, blk), blk, 0, s>>>(P, B.C, B.p, B.ux, B.uy, B.g_out, B.h_out, B.tau_out);
+cudaError_t launch_planes_from_f64(const DevParams &P, const double *src, float *dst, int nplanes, cudaStream_t s) {
+  return launch_planes_from_f64_rows(P, src, dst, nplanes, 0, P.ny, s);
 }
+
+// Initial equilibria of rows [y0, y1) (they read C and p two rows beyond).
+void launch_init_rows(const DevParams &P, const StepBuffers &B, int y0, int y1, cudaStream_t s) {
+  const dim3 blk(32, 8);
+  const dim3 grd((P.nx + blk.x - 1) / blk.x, (y1 - y0 + blk.y - 1) / blk.y);
+  if (y1 <= y0) return;
+  if (P.nh == 1)
+    k_init<1><<<grd, blk, 0, s>>>(P, B.C, B.p, B.ux, B.uy, B.g_out, B.h_out, B.tau_out, y0, y1);
+  else
+    k_init<2><<<grd, blk, 0, s>>>(P, B.C, B.p, B.ux, B.uy, B.g_out, B.h_out, B.tau_out, y0, y1);
+}
+
+void launch_init(const DevParams &P, const StepBuffers &B, cudaStream_t s) { launch_init_rows(P, B, 0, P.ny, s); }
 
 void launch_moments(const DevParams &P, const float *h, float *C, cudaStream_t s) {
   const dim3 blk(32, 8);
