@@ -161,7 +161,11 @@ lbm_status lbm_init_bubbles(lbm_handle *h, const lbm_bubble *bubbles, int nb, un
  * modified equilibria of Eq. 16 and Eq. 20; tau uses a zero strain rate.  The
  * doubles are copied to the device as they are (through the spare population
  * buffer) and rounded to FP32 there; page-locked host memory makes the copy
- * faster.  Synchronises the stream. */
+ * faster.  With FP32 populations, at least 64 rows and a stream that is not
+ * being captured, C goes up in row chunks on a second stream that the handle
+ * creates on first use (and destroys with the handle), overlapped with the
+ * conversion and the equilibria on the handle's stream.  Synchronises the
+ * stream; returns when every copy is done. */
 lbm_status lbm_set_fields(lbm_handle *h, const double *C, const double *p, const double *ux,
                           const double *uy);
 
