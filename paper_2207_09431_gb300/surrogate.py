@@ -115,13 +115,13 @@ class TerminalStateModel:
 
 
 def evaluate(n_train=1024, n_test=128, grid=(100, 200), members=5, epochs=1000, max_steps=30000, seed=1000,
-             test_seed=9000, stream=None, max_spread=0.05, return_model=False):
+             test_seed=9000, stream=None, max_spread=0.05, return_model=False, density_ratio=100.0):
     """Trains on solver terminal states of n_train seeded cases and judges the
     network on n_test held-out cases solved in full.  Returns a summary dict:
     C_D error of the network on every converged test case and on the trusted
     ones, the fallback count, and the time to answer with and without the
     network (and the trained model if return_model)."""
-    train = inputs.ensemble_cases(n_train, seed=seed, grids=(grid,))
+    train = inputs.ensemble_cases(n_train, seed=seed, grids=(grid,), density_ratio=density_ratio)
     res, wall_train = run_to_terminal(train, max_steps=max_steps, stream=stream)
     keep = [i for i, r in enumerate(res) if r["finite"] and r["converged"] and r["U_t"] > 0 and r["C_D"] > 0]
     X = np.stack([features(train[i][0], train[i][2]) for i in keep])
@@ -130,7 +130,7 @@ def evaluate(n_train=1024, n_test=128, grid=(100, 200), members=5, epochs=1000, 
     model = TerminalStateModel(members=members, seed=seed, max_rows=max(len(keep), 1), max_batch=512,
                                max_spread=max_spread)
     loss = model.fit(X, U, CD, epochs=epochs)
-    test = inputs.ensemble_cases(n_test, seed=test_seed, grids=(grid,))
+    test = inputs.ensemble_cases(n_test, seed=test_seed, grids=(grid,), density_ratio=density_ratio)
     ref, wall_solver = run_to_terminal(test, max_steps=max_steps, stream=stream)
     Xt = np.stack([features(p, m) for p, _, m in test])
     t0 = time.perf_counter()
